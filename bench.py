@@ -1,0 +1,341 @@
+"""Benchmark: BGP queries/s (plain form, one query at a time) on a seeded
+R-MAT RDF graph resident on one B300, with p50/p99 latency, the triple-scan
+roofline and the CPU oracle beside it. Prints one JSON line on rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat22]
+                    [--impl gsmart|reference]
+
+A step evaluates every query of the workload once, one after another:
+plan on the host, evaluate on the device, wait for the answer count (the
+answer rows stay on the device). `e2e` is the same step through the public
+API with the answer rows fetched into pinned host memory. With N > 1
+(torchrun) every rank holds its own copy of the graph and runs the whole
+query list (replicas: queries are independent, there is no exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import rdfgen  # noqa: E402
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="rmat22")
+    ap.add_argument("--impl", default="gsmart", choices=["gsmart", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="budget of the CPU oracle sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(name):
+    w = rdfgen.WORKLOADS[name]
+    s, p, o = rdfgen.graph(w)
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    qs = rdfgen.queries(w, sm)
+    sm.close()
+    return w, (s, p, o), qs
+
+
+def _cpu_baseline(w, triples, qs, budget_s):
+    """The oracle as it stands, on all host cores, on a bounded sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ix = oracle.Index(*triples, w.n_vertices, w.n_preds)
+    build_s = time.perf_counter() - t0
+    done, rows, t0 = 0, 0, time.perf_counter()
+    for q in qs:
+        rows += len(ix.eval(q.patterns, threads=cores))
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d of %d queries of %s, one at a time, %d answer rows; "
+                      "index build %.1f s excluded" % (done, len(qs), w.name, rows, build_s)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    w, triples, qs = _workload(args.workload)
+    import oracle
+    cores = os.cpu_count() or 1
+    ix = oracle.Index(*triples, w.n_vertices, w.n_preds)
+    # each step: a bounded prefix of the query list, sized so the run ends in minutes
+    budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    n_q = len(qs)
+    t0 = time.perf_counter()
+    for i, q in enumerate(qs):
+        ix.eval(q.patterns, threads=cores)
+        if time.perf_counter() - t0 > budget:
+            n_q = i + 1
+            break
+    sample = qs[:n_q]
+    for _ in range(args.warmup):
+        for q in sample:
+            ix.eval(q.patterns, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for q in sample:
+            ix.eval(q.patterns, threads=cores)
+    dt = time.perf_counter() - t0
+    v = args.steps * len(sample) / dt
+    desc = "first %d of %d queries of %s per step" % (len(sample), len(qs), w.name)
+    print(json.dumps({
+        "impl": "reference", "metric": "BGP queries/s (plain, one at a time)", "value": v,
+        "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w.name, "scale": w.scale, "triples_drawn": w.n_edges,
+                   "predicates": w.n_preds, "queries": len(qs)},
+        "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_gsmart(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    import paper_2106_14038_b300 as gs
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w, triples, qs = _workload(args.workload)
+    g = gs.Graph(*triples, w.n_vertices, w.n_preds)
+    stream = torch.cuda.current_stream()
+    plans = None
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
+
+    def step(fetch: bool, lat=None, out_bufs=None):
+        launches, d2h, h2d = 0, 0, 0
+        for i, q in enumerate(qs):
+            t0 = time.perf_counter()
+            plan = g.plan(q.patterns)
+            r = g.eval(plan, stream)
+            n, k = r.info()
+            if fetch:
+                buf = out_bufs[i]
+                r.fetch(sort=False, out=buf[: n * k].view(n, k).numpy())
+                d2h += 4 * n * k
+                h2d += q.patterns.nbytes
+            if lat is not None:
+                lat.append(time.perf_counter() - t0)
+            launches += r.stats()[1]
+            r.close()
+            plan.close()
+        return launches, h2d, d2h
+
+    # pinned host buffers for the end-to-end answers (sized by one untimed run)
+    sizes = []
+    for q in qs:
+        r = g.eval(q.patterns, stream)
+        n, k = r.info()
+        sizes.append(max(1, n * k))
+        r.close()
+    out_bufs = [torch.empty(sz, dtype=torch.int32, pin_memory=True) for sz in sizes]
+
+    for _ in range(args.warmup):
+        step(False)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = []
+    step_ms = []
+    launches = 0
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            barrier()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            launches, _, _ = step(False, lat)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            step_ms.append(ev0.elapsed_time(ev1))
+    clocks = clk.summary()
+    t_ms = float(np.sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = ws * len(qs) * args.steps / (t_ms / 1000.0)
+
+    # end to end: same step with answers copied into pinned host memory
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, h2d, d2h = step(True, None, out_bufs)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+    e2e_total = float(np.sum(e2e_ms))
+    if dist is not None:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = ws * len(qs) * args.steps / (e2e_total / 1000.0)
+
+    # triple scan (Eq. 17 / Eq. 21 over the whole matrix): the bandwidth kernel
+    peaks, which = _peaks()
+    preds = [1, 2, 3, 1, 2]
+    dirs = [0, 0, 0, 1, 1]
+    words = (w.n_vertices + 31) // 32
+    out = torch.empty(words, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        g.scan(preds, dirs, out=out)
+    n_scan = 20
+    se0, se1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    scan_ms = 0.0
+    for _ in range(n_scan):
+        flush.fill_(1)
+        se0.record(stream)
+        g.scan(preds, dirs, out=out)
+        se1.record(stream)
+        torch.cuda.synchronize()
+        scan_ms += se0.elapsed_time(se1)
+    scan_ms /= n_scan
+    N, M = w.n_vertices, g.n_triples
+    alg_bytes = 2 * (4 * (N + 1) + 4 * M) + N // 8
+    achieved = alg_bytes / (scan_ms / 1000.0) / 1e9
+    roof = {"kernel": "triple scan (gs_scan_candidates: rows pass + columns pass)",
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_source": which,
+            "traffic": None, "algorithmic_bytes": alg_bytes, "ms_per_launch": scan_ms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = _cpu_baseline(w, triples, qs, args.cpu_seconds)
+
+    if rank == 0:
+        lat_ms = 1000 * np.array(lat)
+        print(json.dumps({
+            "metric": "BGP queries/s (plain, one at a time)", "value": value,
+            "unit": "queries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": w.name, "scale": w.scale, "triples_drawn": w.n_edges,
+                       "triples": M, "predicates": w.n_preds, "queries": len(qs),
+                       "l2": "flushed before every step (256 MiB write); graph %.2f GB > L2"
+                             % ((8 * (N + 1) + 16 * M) / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": launches * args.steps,
+        }), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gsmart(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * gsmart.h — C ABI of the B300 engine for SPARQL basic graph patterns by
+ * grouped incident-edge evaluation over a sparse RDF matrix.
+ *
+ * Model (paper Sec. 1, Sec. 2.2): an RDF data set of M triples (s, p, o) is
+ * an N x N sparse matrix A whose entry A(s, o) is the predicate id p. Vertex
+ * ids are 0-based and predicate ids 1-based, 0 meaning "no entry"
+ * (Sec. 6.2.1 step 2). Several predicates between one (s, o) pair are
+ * several entries. A query is a basic graph pattern: a set of triple
+ * patterns whose subject / object is a constant vertex or a variable and
+ * whose predicate is a constant (Sec. 2.2.1); its answer is the set of
+ * variable bindings that satisfy all patterns together (Sec. 2.2.3).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a gs_status and never aborts, traps or exits.
+ *     gs_last_error() returns a message for the calling thread's last
+ *     failure (valid until that thread's next call).
+ *   - "cuda_stream" is a cudaStream_t passed as void*; NULL is the legacy
+ *     default stream. Work is enqueued on it; calls that must see results
+ *     synchronize it and say so.
+ *   - Inputs are copied in; the caller keeps ownership of its buffers.
+ *     Objects returned through an out-pointer belong to the caller, who
+ *     releases them with the matching gs_free_* call (NULL is accepted).
+ *   - Device memory comes from the gs_allocator when one is given (for
+ *     example a framework's caching allocator), else from stream-ordered
+ *     cudaMallocAsync.
+ *   - Not thread-safe per object: one object must not be used by two host
+ *     threads at once. Distinct objects may be used concurrently.
+ */
+#ifndef GSMART_H
+#define GSMART_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gs_graph gs_graph;
+typedef struct gs_plan gs_plan;
+typedef struct gs_result gs_result;
+
+typedef enum {
+    GS_OK = 0,
+    GS_EINVAL = 1,     /* bad argument, triple or query */
+    GS_ENOMEM = 2,     /* device or host allocation failed */
+    GS_ECUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error) */
+    GS_EOVERFLOW = 4,  /* a caller buffer is too small (nothing written) */
+    GS_ETIMEOUT = 5,   /* a bounded device-side wait ran out */
+    GS_ENOTIMPL = 6    /* feature not available in this build */
+} gs_status;
+
+/* Device allocation hook. alloc returns NULL on failure; both run on the
+ * host thread that made the library call, with the stream the memory is
+ * used on. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* cuda_stream, void* ctx);
+    void (*free)(void* ptr, void* cuda_stream, void* ctx);
+    void* ctx;
+} gs_allocator;
+
+/* ------------------------------------------------------------------ */
+/* Store (Sec. 6.2, LSpM): the RDF matrix resident on the device twice,
+ * row-wise (CSR, rows = subjects) and column-wise (CSC, columns =
+ * objects). Every stored nonzero carries its uint32 predicate label.
+ * Within a row the entries are sorted by (label, column), within a column
+ * by (label, row), so the entries of one predicate in one row / column
+ * form one contiguous, sorted range. Exact duplicate triples are dropped.
+ * Unlike the paper's per-query LSpM, no predicate or empty row is
+ * dropped: one store serves every query.
+ *
+ *   s, p, o            n triples; host pointers, or device pointers when
+ *                      inputs_on_device != 0
+ *   n_vertices         N: every s and o must be < N; N <= 2^31
+ *   n_predicates       P: every p must be in 1..P
+ *   alloc              optional allocation hook (copied; ctx must outlive
+ *                      the graph)
+ * Synchronizes cuda_stream. GS_EINVAL on a bad triple, N = 0, P = 0, or
+ * when 2*ceil(log2 N) + ceil(log2 (P+1)) > 64 (packed sort keys). */
+gs_status gs_load_triples(const uint32_t* s, const uint32_t* p, const uint32_t* o, uint64_t n,
+                          uint32_t n_vertices, uint32_t n_predicates, int inputs_on_device,
+                          const gs_allocator* alloc, void* cuda_stream, gs_graph** out);
+
+/* Sizes of a loaded graph: M (after deduplication), N, P. Any out pointer
+ * may be NULL. */
+gs_status gs_graph_info(const gs_graph* g, uint64_t* n_triples, uint32_t* n_vertices,
+                        uint32_t* n_predicates);
+
+/* Copy one orientation of the store out (for inspection and tests).
+ *   by_column = 0: ptr[N+1] row pointers, idx[M] object of each entry,
+ *                  lab[M] predicate; entries grouped by subject
+ *   by_column = 1: the column-wise copy: ptr by object, idx = subject
+ * Buffers are host memory unless dst_on_device. Synchronizes cuda_stream. */
+gs_status gs_graph_export(const gs_graph* g, int by_column, uint32_t* ptr, uint32_t* idx,
+                          uint32_t* lab, int dst_on_device, void* cuda_stream);
+
+/* ------------------------------------------------------------------ */
+/* Planner (Sec. 6.1): the query graph and the order in which the
+ * incident edges of its vertices are evaluated, group by group.
+ *
+ *   patterns     n_patterns x 3 int64 in row order (s, p, o), host memory:
+ *                s, o >= 0 is a constant vertex id (< N); s, o < 0 is the
+ *                variable -(k+1), variables numbered densely 0..K-1;
+ *                p is a predicate id in 1..P
+ *   flags        GS_PLAN_DEGREE (Sec. 6.1.2, the default) or
+ *                GS_PLAN_DIRECTION (Sec. 6.1.1; queries with constants
+ *                use the degree-driven order, as the paper prescribes)
+ * g may be NULL: the plan is then made without a graph and its ids are
+ * checked by gs_eval_query against the graph it runs on.
+ * GS_EINVAL when there is no variable, the variables are not dense, an id
+ * is out of range, or n_patterns > GS_MAX_PATTERNS; GS_ENOTIMPL when a
+ * variable has more than 8 distinct patterns to bound ends or 8 self-loops, or a
+ * scan would test more than 31 distinct predicates in one direction.
+ * Host only. */
+#define GS_PLAN_DEGREE 0u
+#define GS_PLAN_DIRECTION 1u
+#define GS_MAX_PATTERNS 32
+#define GS_MAX_VARS 31
+gs_status gs_plan_query(const gs_graph* g, const int64_t* patterns, uint32_t n_patterns,
+                        uint32_t flags, gs_plan** out);
+
+/* The plan as int32 words, for inspection:
+ *   [n_groups, then per group: vertex, n_edges, edge indices...,
+ *    n_roots, roots...]
+ * where a vertex is the variable index k >= 0, or -(1 + c) for constant
+ * vertex id c. *len receives the word count; GS_EOVERFLOW (nothing
+ * written) when cap is smaller. */
+gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint32_t* len);
+
+/* ------------------------------------------------------------------ */
+/* Evaluation (Sec. 5, Sec. 7): grouped incident-edge evaluation of the
+ * plan, fully on the device. Candidate vectors of the variables are the
+ * AND of the predicate selections of all their incident edges (Eq. 17,
+ * Eq. 21); bindings are expanded level by level into a tree stored as
+ * device arrays (Sec. 7.1), pruned as soon as an edge has no match
+ * (Sec. 7.2.2) and enumerated into tuples.
+ *
+ * gs_eval_query enqueues the work on cuda_stream and returns without
+ * waiting. The result holds device memory until gs_free_result. */
+gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out);
+
+/* Number of answer rows and variables. Synchronizes the result's stream.
+ * When the evaluation ran out of its device workspace it is re-run with a
+ * larger one; GS_ENOMEM when the device cannot hold it. The first
+ * workspace is 512 MiB (at most 1/8 of free memory), or the byte count in
+ * the environment variable GS_ARENA_BYTES. */
+gs_status gs_result_info(gs_result* r, uint64_t* n_rows, uint32_t* n_vars);
+
+/* Copy the answers out: n_rows x n_vars int32, row-major, column k holds
+ * variable k. Rows are distinct; with sort_rows != 0 they are in ascending
+ * lexicographic order, else in an unspecified order. dst is host memory
+ * unless dst_on_device. GS_EOVERFLOW (nothing written) when
+ * cap_rows < n_rows. Synchronizes the result's stream. */
+gs_status gs_fetch_bindings(gs_result* r, int32_t* dst, uint64_t cap_rows, int dst_on_device,
+                            int sort_rows);
+
+/* Statistics of the last evaluation of r (synchronizes): device time in
+ * milliseconds from CUDA events around the enqueued work, and the number of
+ * kernels it launched. Either out pointer may be NULL. */
+gs_status gs_result_stats(gs_result* r, float* device_ms, uint32_t* kernel_launches);
+
+/* ------------------------------------------------------------------ */
+/* One grouped predicate selection on its own (Eq. 17, Eq. 21):
+ *     v = AND_i  (dir_i == 0 ? A (x) u_{p_i} : A^T (x) u_{p_i})
+ * i.e. bit x of v is 1 when row x of A holds every predicate p_i with
+ * dir_i == 0 and column x holds every p_i with dir_i == 1 (Eq. 4, Eq. 5).
+ *   preds, dirs   n host arrays, 1 <= n <= 31 per direction
+ *   out_bits      device buffer of ceil(N/32) uint32 words; bit x of the
+ *                 vector is bit (x % 32) of word x / 32; bits >= N are 0
+ * Enqueued on cuda_stream (no synchronization). */
+gs_status gs_scan_candidates(gs_graph* g, const uint32_t* preds, const uint8_t* dirs, uint32_t n,
+                             uint32_t* out_bits, void* cuda_stream);
+
+void gs_free_graph(gs_graph* g);
+void gs_free_plan(gs_plan* plan);
+void gs_free_result(gs_result* r);
+
+const char* gs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSMART_H */

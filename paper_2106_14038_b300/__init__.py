@@ -1,0 +1,276 @@
+"""B300 engine for SPARQL basic graph patterns by grouped incident-edge
+evaluation over a sparse RDF matrix (gSmart, arXiv 2106.14038).
+
+Thin ctypes binding over libgsmart.so (include/gsmart.h): argument
+marshalling only; every step of the evaluation runs in the library's CUDA
+kernels. PyTorch supplies CUDA streams and device tensors. There is no CPU
+fallback: without the built library, or without a GPU, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB, build
+
+__all__ = ["Graph", "Plan", "Result", "GsError", "load_library", "PLAN_DEGREE",
+           "PLAN_DIRECTION", "build"]
+
+PLAN_DEGREE = 0
+PLAN_DIRECTION = 1
+_STATUS = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOMEM", 3: "GS_ECUDA", 4: "GS_EOVERFLOW",
+           5: "GS_ETIMEOUT", 6: "GS_ENOTIMPL"}
+
+EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_query",
+            "gs_plan_describe", "gs_eval_query", "gs_result_info", "gs_fetch_bindings",
+            "gs_result_stats", "gs_scan_candidates", "gs_free_graph", "gs_free_plan",
+            "gs_free_result", "gs_last_error"]
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libgsmart.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise ImportError("libgsmart.so is not built; run paper_2106_14038_b300.build() "
+                          "(nvcc for sm_103a)")
+    lib = ctypes.CDLL(path)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "gs_load_triples": [vp, vp, vp, u64, u32, u32, i32, vp, vp, P(vp)],
+        "gs_graph_info": [vp, P(u64), P(u32), P(u32)],
+        "gs_graph_export": [vp, i32, vp, vp, vp, i32, vp],
+        "gs_plan_query": [vp, vp, u32, u32, P(vp)],
+        "gs_plan_describe": [vp, vp, u32, P(u32)],
+        "gs_eval_query": [vp, vp, vp, P(vp)],
+        "gs_result_info": [vp, P(u64), P(u32)],
+        "gs_fetch_bindings": [vp, vp, u64, i32, i32],
+        "gs_result_stats": [vp, P(ctypes.c_float), P(u32)],
+        "gs_scan_candidates": [vp, vp, vp, u32, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = i32
+    for name in ("gs_free_graph", "gs_free_plan", "gs_free_result"):
+        f = getattr(lib, name)
+        f.argtypes = [vp]
+        f.restype = None
+    lib.gs_last_error.argtypes = []
+    lib.gs_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise GsError(rc, _lib.gs_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _host_u32(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.uint32)
+
+
+class Graph:
+    """The RDF matrix resident on the device (CSR + CSC with labels)."""
+
+    def __init__(self, s, p, o, n_vertices: int, n_predicates: int, stream=None):
+        lib = load_library()
+        self._keep = None
+        on_dev = hasattr(s, "is_cuda") and s.is_cuda
+        if on_dev:
+            import torch
+            s, p, o = (x.to(torch.int32).contiguous() for x in (s, p, o))
+            ptrs = [ctypes.c_void_p(x.data_ptr()) for x in (s, p, o)]
+            n = s.numel()
+            self._keep = (s, p, o)
+        else:
+            s, p, o = _host_u32(s), _host_u32(p), _host_u32(o)
+            ptrs = [x.ctypes.data_as(ctypes.c_void_p) for x in (s, p, o)]
+            n = len(s)
+            self._keep = (s, p, o)
+        h = ctypes.c_void_p()
+        _check(lib.gs_load_triples(*ptrs, n, n_vertices, n_predicates, int(on_dev), None,
+                                   _stream_handle(stream), ctypes.byref(h)))
+        self._keep = None
+        self._h = h
+        self.n_vertices, self.n_predicates = int(n_vertices), int(n_predicates)
+        m = ctypes.c_uint64()
+        _check(lib.gs_graph_info(h, ctypes.byref(m), None, None))
+        self.n_triples = int(m.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.gs_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self, by_column: bool = False, stream=None):
+        """(ptr, idx, lab) numpy arrays of the row-wise (or column-wise) copy."""
+        ptr = np.empty(self.n_vertices + 1, np.uint32)
+        idx = np.empty(max(self.n_triples, 1), np.uint32)
+        lab = np.empty(max(self.n_triples, 1), np.uint32)
+        _check(_lib.gs_graph_export(self._h, int(by_column), ptr.ctypes.data_as(ctypes.c_void_p),
+                                    idx.ctypes.data_as(ctypes.c_void_p),
+                                    lab.ctypes.data_as(ctypes.c_void_p), 0, _stream_handle(stream)))
+        return ptr, idx[:self.n_triples], lab[:self.n_triples]
+
+    def plan(self, patterns, flags: int = PLAN_DEGREE) -> "Plan":
+        return Plan(self, patterns, flags)
+
+    def eval(self, plan_or_patterns, stream=None) -> "Result":
+        plan = plan_or_patterns if isinstance(plan_or_patterns, Plan) else self.plan(plan_or_patterns)
+        h = ctypes.c_void_p()
+        _check(_lib.gs_eval_query(self._h, plan._h, _stream_handle(stream), ctypes.byref(h)))
+        return Result(h, plan)
+
+    def query(self, patterns, sort: bool = True, flags: int = PLAN_DEGREE, stream=None):
+        """Answer rows (numpy int32, n_rows x n_vars) of a BGP."""
+        r = self.eval(self.plan(patterns, flags), stream)
+        try:
+            return r.fetch(sort=sort)
+        finally:
+            r.close()
+
+    def scan(self, preds, dirs, out=None, stream=None):
+        """Eq. 17 / Eq. 21 on its own: a torch int32 tensor of ceil(N/32)
+        words, bit x set when row x holds every preds[i] with dirs[i] == 0
+        and column x every preds[i] with dirs[i] == 1."""
+        import torch
+        words = (self.n_vertices + 31) // 32
+        if out is None:
+            out = torch.empty(words, dtype=torch.int32, device="cuda")
+        pr = _host_u32(preds)
+        dr = np.ascontiguousarray(np.asarray(dirs), dtype=np.uint8)
+        _check(_lib.gs_scan_candidates(self._h, pr.ctypes.data_as(ctypes.c_void_p),
+                                       dr.ctypes.data_as(ctypes.c_void_p), len(pr),
+                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+
+class Plan:
+    def __init__(self, graph: Graph, patterns, flags: int = PLAN_DEGREE):
+        load_library()
+        pat = np.ascontiguousarray(np.asarray(patterns, dtype=np.int64).reshape(-1, 3))
+        h = ctypes.c_void_p()
+        _check(_lib.gs_plan_query(graph._h, pat.ctypes.data_as(ctypes.c_void_p), len(pat),
+                                  flags, ctypes.byref(h)))
+        self._h = h
+        self.patterns = pat
+        self.n_vars = int(-pat[:, [0, 2]][pat[:, [0, 2]] < 0].min()) if (pat[:, [0, 2]] < 0).any() else 0
+
+    def describe(self):
+        """(groups, roots): groups = [(vertex, [edge indices])]; a vertex is a
+        variable index k >= 0 or ('c', id) for a constant."""
+        n = ctypes.c_uint32()
+        _lib.gs_plan_describe(self._h, None, 0, ctypes.byref(n))
+        buf = np.zeros(n.value, np.int32)
+        _check(_lib.gs_plan_describe(self._h, buf.ctypes.data_as(ctypes.c_void_p), n.value,
+                                     ctypes.byref(n)))
+        w = buf.tolist()
+
+        def vert(x):
+            return x if x >= 0 else ("c", -x - 1)
+
+        i = 0
+        ng = w[i]; i += 1
+        groups = []
+        for _ in range(ng):
+            v, ne = w[i], w[i + 1]
+            groups.append((vert(v), w[i + 2:i + 2 + ne]))
+            i += 2 + ne
+        nr = w[i]; i += 1
+        roots = [vert(x) for x in w[i:i + nr]]
+        return groups, roots
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.gs_free_plan(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Result:
+    def __init__(self, h, plan: Plan):
+        self._h = h
+        self._plan = plan
+
+    def info(self):
+        n = ctypes.c_uint64()
+        k = ctypes.c_uint32()
+        _check(_lib.gs_result_info(self._h, ctypes.byref(n), ctypes.byref(k)))
+        return int(n.value), int(k.value)
+
+    def stats(self):
+        """(device milliseconds of the last evaluation, kernels it launched)."""
+        ms = ctypes.c_float()
+        n = ctypes.c_uint32()
+        _check(_lib.gs_result_stats(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return float(ms.value), int(n.value)
+
+    def time_ms(self) -> float:
+        return self.stats()[0]
+
+    def fetch(self, sort: bool = True, out=None):
+        """Answer rows. out: None (a new numpy array), a numpy int32 array,
+        or a torch CUDA int32 tensor (device-to-device copy)."""
+        n, k = self.info()
+        if out is None:
+            out = np.empty((n, k), np.int32)
+        on_dev = hasattr(out, "is_cuda") and out.is_cuda
+        if on_dev:
+            ptr = ctypes.c_void_p(out.data_ptr())
+            cap = out.numel() // max(k, 1)
+        else:
+            ptr = out.ctypes.data_as(ctypes.c_void_p)
+            cap = out.size // max(k, 1)
+        _check(_lib.gs_fetch_bindings(self._h, ptr, cap, int(on_dev), int(sort)))
+        return out if on_dev else out[:n]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.gs_free_result(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,401 @@
+// The C ABI (include/gsmart.h): argument checks, object lifetimes, the
+// workspace retry loop and the device row sort used by gs_fetch_bindings.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "gs_device.cuh"
+#include "gs_exec.h"
+
+namespace gs {
+const char* last_error();
+}
+
+using namespace gs;
+
+struct gs_result {
+    gs_graph* g = nullptr;
+    gs_plan plan;
+    cudaStream_t st = nullptr;
+    uint8_t* arena = nullptr;
+    uint64_t arena_bytes = 0;
+    uint32_t* bits = nullptr;
+    void* work = nullptr;
+    uint32_t* lists = nullptr;
+    uint64_t list_stride = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool ready = false;
+    uint32_t launches = 0;
+    uint64_t rows = 0;
+    uint64_t out_off = 0;
+};
+
+namespace {
+
+constexpr uint64_t kArenaMin = 64ull << 20;
+constexpr uint64_t kArenaDefault = 512ull << 20;
+constexpr int kMaxRetries = 16;
+
+ExecDev exec_view(gs_result* r) {
+    ExecDev E{};
+    E.arena = r->arena;
+    E.arena_bytes = r->arena_bytes;
+    E.ctl = (Ctl*)r->arena;
+    E.out = dview(r->g->out);
+    E.in = dview(r->g->in);
+    E.bits = r->bits;
+    E.words = (r->g->N + 31) / 32;
+    E.lists = r->lists;
+    E.list_stride = r->list_stride;
+    return E;
+}
+
+gs_status enqueue(gs_result* r) {
+    GS_CUDA(cudaEventRecord(r->ev0, r->st));
+    gs_status rc = enqueue_eval(r->g, &r->plan, exec_view(r), r->work, &r->launches, r->st);
+    if (rc != GS_OK) return rc;
+    GS_CUDA(cudaEventRecord(r->ev1, r->st));
+    r->ready = false;
+    return GS_OK;
+}
+
+gs_status wait_result(gs_result* r) {
+    if (r->ready) return GS_OK;
+    for (int attempt = 0; attempt < kMaxRetries; ++attempt) {
+        GS_CUDA(cudaStreamSynchronize(r->st));
+        Ctl head;
+        GS_CUDA(cudaMemcpy(&head, r->arena, kCtlHead, cudaMemcpyDeviceToHost));
+        if (head.status & kStHuge) {
+            set_error("gs_eval_query: the answer has more than 2^40 rows under one binding");
+            return GS_ENOMEM;
+        }
+        if (!(head.status & kStOverflow)) {
+            const int last = r->plan.n_levels - 1;
+            r->rows = head.rows;
+            r->out_off = host_level_off(head.n, last + 1);
+            r->ready = true;
+            return GS_OK;
+        }
+        // workspace too small: grow it and run again
+        uint64_t need = kCtlBytes;
+        for (int l = 0; l < r->plan.n_levels; ++l) need += 8 * head.n[l] + 256;
+        need += 4ull * head.rows * r->plan.n_vars;
+        uint64_t nb = std::max<uint64_t>(r->arena_bytes * 4, need * 2);
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        r->g->alloc.put(r->arena, r->st);
+        r->arena = nullptr;
+        GS_CUDA(cudaStreamSynchronize(r->st));
+        cudaMemGetInfo(&free_b, &total_b);
+        if (nb > (uint64_t)free_b * 9 / 10) nb = (uint64_t)free_b * 9 / 10;
+        if (nb <= r->arena_bytes) {
+            set_error("gs_eval_query: the evaluation needs more device memory than is free");
+            return GS_ENOMEM;
+        }
+        r->arena = (uint8_t*)r->g->alloc.get(nb, r->st);
+        if (!r->arena) { set_error("gs_eval_query: cannot allocate a %llu-byte workspace", (unsigned long long)nb); return GS_ENOMEM; }
+        r->arena_bytes = nb;
+        gs_status rc = enqueue(r);
+        if (rc != GS_OK) return rc;
+    }
+    set_error("gs_eval_query: workspace retries exhausted");
+    return GS_ENOMEM;
+}
+
+void release(gs_result* r) {
+    if (!r) return;
+    if (r->g) {
+        cudaStreamSynchronize(r->st);
+        r->g->alloc.put(r->arena, r->st);
+        r->g->alloc.put(r->bits, r->st);
+        r->g->alloc.put(r->work, r->st);
+        r->g->alloc.put(r->lists, r->st);
+    }
+    if (r->ev0) cudaEventDestroy(r->ev0);
+    if (r->ev1) cudaEventDestroy(r->ev1);
+    delete r;
+}
+
+// ---- device row sort (lexicographic, LSD over columns) ----
+
+__global__ void k_sort_keys(const int32_t* __restrict__ rows, uint32_t k, uint32_t c, uint64_t n,
+                            uint64_t* __restrict__ keys, int first) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t perm = first ? i : (keys[i] & 0xffffffffull);
+        uint32_t v = (uint32_t)rows[perm * k + c];
+        keys[i] = ((uint64_t)v << 32) | perm;
+    }
+}
+
+__global__ void k_sort_gather(const int32_t* __restrict__ rows, uint32_t k, uint64_t n,
+                              const uint64_t* __restrict__ keys, int32_t* __restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t perm = keys[i] & 0xffffffffull;
+        for (uint32_t j = 0; j < k; ++j) out[i * k + j] = rows[perm * k + j];
+    }
+}
+
+gs_status sort_rows_dev(const gs_graph* g, const int32_t* rows, uint64_t n, uint32_t k,
+                        int32_t* out, cudaStream_t st) {
+    if (n >= (1ull << 32)) { set_error("gs_fetch_bindings: sorting needs fewer than 2^32 rows"); return GS_ENOTIMPL; }
+    uint64_t* k0 = (uint64_t*)g->alloc.get(8 * n, st);
+    uint64_t* k1 = (uint64_t*)g->alloc.get(8 * n, st);
+    if (!k0 || !k1) { g->alloc.put(k0, st); g->alloc.put(k1, st); set_error("gs_fetch_bindings: out of device memory for sorting"); return GS_ENOMEM; }
+    const int nb = g->n_blocks;
+    gs_status rc = GS_OK;
+    for (int c = (int)k - 1; c >= 0 && rc == GS_OK; --c) {
+        k_sort_keys<<<nb, kThreads, 0, st>>>(rows, k, (uint32_t)c, n, k0, c == (int)k - 1);
+        rc = radix_sort_u64(g, &k0, &k1, n, 32, 64, st);
+    }
+    if (rc == GS_OK) k_sort_gather<<<nb, kThreads, 0, st>>>(rows, k, n, k0, out);
+    cudaError_t e = cudaGetLastError();
+    g->alloc.put(k0, st);
+    g->alloc.put(k1, st);
+    if (rc == GS_OK && e != cudaSuccess) rc = cuda_fail(e, "row sort");
+    return rc;
+}
+
+void set_pool_threshold(int dev) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gs_last_error(void) { return last_error(); }
+
+gs_status gs_load_triples(const uint32_t* s, const uint32_t* p, const uint32_t* o, uint64_t n,
+                          uint32_t n_vertices, uint32_t n_predicates, int inputs_on_device,
+                          const gs_allocator* alloc, void* cuda_stream, gs_graph** out) {
+    if (!out) { set_error("gs_load_triples: out is NULL"); return GS_EINVAL; }
+    *out = nullptr;
+    if (n && (!s || !p || !o)) { set_error("gs_load_triples: NULL triple array"); return GS_EINVAL; }
+    if (n_vertices == 0 || n_vertices > (1u << 31)) { set_error("gs_load_triples: n_vertices must be in 1..2^31"); return GS_EINVAL; }
+    if (n_predicates == 0 || n_predicates > 65535) { set_error("gs_load_triples: n_predicates must be in 1..65535"); return GS_EINVAL; }
+    if (alloc && (!alloc->alloc || !alloc->free)) { set_error("gs_load_triples: allocator needs alloc and free"); return GS_EINVAL; }
+    int dev = 0;
+    GS_CUDA(cudaGetDevice(&dev));
+    gs_graph* g = new (std::nothrow) gs_graph();
+    if (!g) { set_error("gs_load_triples: host out of memory"); return GS_ENOMEM; }
+    g->N = n_vertices;
+    g->P = n_predicates;
+    g->device = dev;
+    if (alloc) { g->alloc.hook = *alloc; g->alloc.has_hook = true; }
+    cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    g->n_blocks = std::min(kBlocks, std::max(1, g->sm_count * 4));
+    set_pool_threshold(dev);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    gs_status rc = build_store(g, s, p, o, n, inputs_on_device != 0, st);
+    if (rc != GS_OK) {
+        free_store(g, st);
+        cudaStreamSynchronize(st);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return GS_OK;
+}
+
+gs_status gs_graph_info(const gs_graph* g, uint64_t* n_triples, uint32_t* n_vertices,
+                        uint32_t* n_predicates) {
+    if (!g) { set_error("gs_graph_info: graph is NULL"); return GS_EINVAL; }
+    if (n_triples) *n_triples = g->M;
+    if (n_vertices) *n_vertices = g->N;
+    if (n_predicates) *n_predicates = g->P;
+    return GS_OK;
+}
+
+gs_status gs_graph_export(const gs_graph* g, int by_column, uint32_t* ptr, uint32_t* idx,
+                          uint32_t* lab, int dst_on_device, void* cuda_stream) {
+    if (!g || !ptr || !idx || !lab) { set_error("gs_graph_export: NULL argument"); return GS_EINVAL; }
+    const Store& S = by_column ? g->in : g->out;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    GS_CUDA(cudaMemcpyAsync(ptr, S.ptr, sizeof(uint32_t) * ((uint64_t)g->N + 1), kind, st));
+    if (g->M) {
+        GS_CUDA(cudaMemcpyAsync(idx, S.idx, sizeof(uint32_t) * g->M, kind, st));
+        GS_CUDA(cudaMemcpyAsync(lab, S.lab, sizeof(uint32_t) * g->M, kind, st));
+    }
+    GS_CUDA(cudaStreamSynchronize(st));
+    return GS_OK;
+}
+
+gs_status gs_plan_query(const gs_graph* g, const int64_t* patterns, uint32_t n_patterns,
+                        uint32_t flags, gs_plan** out) {
+    if (!out) { set_error("gs_plan_query: out is NULL"); return GS_EINVAL; }
+    return make_plan(g, patterns, n_patterns, flags, out);
+}
+
+gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint32_t* len) {
+    if (!plan || !len) { set_error("gs_plan_describe: NULL argument"); return GS_EINVAL; }
+    std::vector<int32_t> w;
+    w.push_back((int32_t)plan->groups.size());
+    for (auto& gr : plan->groups) {
+        w.push_back((int32_t)gr.first);
+        w.push_back((int32_t)gr.second.size());
+        for (int e : gr.second) w.push_back(e);
+    }
+    w.push_back((int32_t)plan->roots.size());
+    for (int64_t r : plan->roots) w.push_back((int32_t)r);
+    *len = (uint32_t)w.size();
+    if (!buf || cap < w.size()) { set_error("gs_plan_describe: buffer holds %u words, need %zu", cap, w.size()); return GS_EOVERFLOW; }
+    std::memcpy(buf, w.data(), sizeof(int32_t) * w.size());
+    return GS_OK;
+}
+
+gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out) {
+    if (!g || !plan || !out) { set_error("gs_eval_query: NULL argument"); return GS_EINVAL; }
+    *out = nullptr;
+    if (plan->N == 0) {   // planned without a graph: check the ids now
+        for (size_t i = 0; i < plan->patterns.size(); i += 3) {
+            int64_t s = plan->patterns[i], p = plan->patterns[i + 1], o = plan->patterns[i + 2];
+            if (p > (int64_t)g->P || s >= (int64_t)g->N || o >= (int64_t)g->N) {
+                set_error("gs_eval_query: pattern %zu has an id outside this graph", i / 3);
+                return GS_EINVAL;
+            }
+        }
+    } else if (plan->N != g->N || plan->P != g->P) {
+        set_error("gs_eval_query: the plan was made for another graph");
+        return GS_EINVAL;
+    }
+    gs_result* r = new (std::nothrow) gs_result();
+    if (!r) { set_error("gs_eval_query: host out of memory"); return GS_ENOMEM; }
+    r->g = g;
+    r->plan = *plan;
+    r->st = (cudaStream_t)cuda_stream;
+    const uint64_t words = (g->N + 31) / 32;
+    gs_status rc = GS_OK;
+    if (cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    if (rc == GS_OK && plan->needs_scan) {
+        r->bits = (uint32_t*)g->alloc.get(4 * words * std::max(1, plan->n_levels), r->st);
+        r->work = g->alloc.get(scan_work_bytes(g), r->st);
+        if (!r->bits || !r->work) { set_error("gs_eval_query: out of device memory"); rc = GS_ENOMEM; }
+    }
+    bool lists = false;
+    for (int l = 1; l < plan->n_levels; ++l) lists |= plan->levels[l].src == kSrcList;
+    if (rc == GS_OK && lists) {
+        r->list_stride = g->N;
+        r->lists = (uint32_t*)g->alloc.get(4ull * g->N * plan->n_levels, r->st);
+        if (!r->lists) { set_error("gs_eval_query: out of device memory"); rc = GS_ENOMEM; }
+    }
+    if (rc == GS_OK) {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        uint64_t want = std::max<uint64_t>(kArenaMin, std::min<uint64_t>(kArenaDefault, free_b / 8));
+        if (const char* env = getenv("GS_ARENA_BYTES")) {   // initial workspace size
+            unsigned long long v = strtoull(env, nullptr, 10);
+            if (v >= 4096) want = v;
+        }
+        r->arena = (uint8_t*)g->alloc.get(want, r->st);
+        r->arena_bytes = want;
+        if (!r->arena) { set_error("gs_eval_query: cannot allocate the workspace"); rc = GS_ENOMEM; }
+    }
+    if (rc == GS_OK) rc = enqueue(r);
+    if (rc != GS_OK) { release(r); return rc; }
+    *out = r;
+    return GS_OK;
+}
+
+gs_status gs_result_info(gs_result* r, uint64_t* n_rows, uint32_t* n_vars) {
+    if (!r) { set_error("gs_result_info: result is NULL"); return GS_EINVAL; }
+    gs_status rc = wait_result(r);
+    if (rc != GS_OK) return rc;
+    if (n_rows) *n_rows = r->rows;
+    if (n_vars) *n_vars = (uint32_t)r->plan.n_vars;
+    return GS_OK;
+}
+
+gs_status gs_result_stats(gs_result* r, float* device_ms, uint32_t* kernel_launches) {
+    if (!r) { set_error("gs_result_stats: result is NULL"); return GS_EINVAL; }
+    gs_status rc = wait_result(r);
+    if (rc != GS_OK) return rc;
+    if (device_ms) GS_CUDA(cudaEventElapsedTime(device_ms, r->ev0, r->ev1));
+    if (kernel_launches) *kernel_launches = r->launches;
+    return GS_OK;
+}
+
+gs_status gs_fetch_bindings(gs_result* r, int32_t* dst, uint64_t cap_rows, int dst_on_device,
+                            int sort_rows) {
+    if (!r) { set_error("gs_fetch_bindings: result is NULL"); return GS_EINVAL; }
+    gs_status rc = wait_result(r);
+    if (rc != GS_OK) return rc;
+    if (cap_rows < r->rows) {
+        set_error("gs_fetch_bindings: buffer holds %llu rows, the answer has %llu",
+                  (unsigned long long)cap_rows, (unsigned long long)r->rows);
+        return GS_EOVERFLOW;
+    }
+    if (r->rows == 0) return GS_OK;
+    if (!dst) { set_error("gs_fetch_bindings: dst is NULL"); return GS_EINVAL; }
+    const uint32_t k = (uint32_t)r->plan.n_vars;
+    const uint64_t bytes = 4ull * r->rows * k;
+    const int32_t* src = (const int32_t*)(r->arena + r->out_off);
+    cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (sort_rows && r->rows > 1) {
+        int32_t* tmp = (int32_t*)r->g->alloc.get(bytes, r->st);
+        if (!tmp) { set_error("gs_fetch_bindings: out of device memory for sorting"); return GS_ENOMEM; }
+        rc = sort_rows_dev(r->g, src, r->rows, k, tmp, r->st);
+        if (rc == GS_OK) {
+            cudaError_t e = cudaMemcpyAsync(dst, tmp, bytes, kind, r->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(r->st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "gs_fetch_bindings copy");
+        }
+        r->g->alloc.put(tmp, r->st);
+        cudaStreamSynchronize(r->st);
+        return rc;
+    }
+    GS_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, r->st));
+    GS_CUDA(cudaStreamSynchronize(r->st));
+    return GS_OK;
+}
+
+gs_status gs_scan_candidates(gs_graph* g, const uint32_t* preds, const uint8_t* dirs, uint32_t n,
+                             uint32_t* out_bits, void* cuda_stream) {
+    if (!g || !preds || !dirs || !out_bits || n == 0) { set_error("gs_scan_candidates: NULL argument or n == 0"); return GS_EINVAL; }
+    ScanSpec S{};
+    S.n_bvars = 1;
+    S.bvar[0] = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (preds[i] < 1 || preds[i] > g->P || dirs[i] > 1) { set_error("gs_scan_candidates: entry %u: predicate outside 1..P or direction not 0/1", i); return GS_EINVAL; }
+        uint32_t* list = dirs[i] ? S.in_pred : S.out_pred;
+        int32_t& cnt = dirs[i] ? S.n_in : S.n_out;
+        int slot = -1;
+        for (int j = 0; j < cnt; ++j) if (list[j] == preds[i]) slot = j;
+        if (slot < 0) {
+            if (cnt >= kMaxSlots) { set_error("gs_scan_candidates: more than %d predicates in one direction", kMaxSlots); return GS_EINVAL; }
+            list[cnt] = preds[i];
+            slot = cnt++;
+        }
+        (dirs[i] ? S.need_in[0] : S.need_out[0]) |= 1u << slot;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    void* work = g->alloc.get(scan_work_bytes(g), st);
+    if (!work) { set_error("gs_scan_candidates: out of device memory"); return GS_ENOMEM; }
+    gs_status rc = run_scan(g, S, out_bits, work, st);
+    g->alloc.put(work, st);
+    return rc;
+}
+
+void gs_free_graph(gs_graph* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    free_store(g, nullptr);
+    cudaDeviceSynchronize();
+    delete g;
+}
+
+void gs_free_plan(gs_plan* plan) { delete plan; }
+
+void gs_free_result(gs_result* r) { release(r); }
+
+}  // extern "C"

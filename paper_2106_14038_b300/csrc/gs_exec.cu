@@ -1,0 +1,493 @@
+// Executor: grouped incident-edge evaluation of one plan (Sec. 5, Sec. 7).
+//
+// Bindings are kept as a tree in device memory (Sec. 7.1): level l holds
+// one (vertex, parent index) pair per binding of the l-th materialized
+// variable, each node extending the partial binding of its parent. A level
+// is produced from the previous one in four steps, all sized on the device
+// (no host round trip):
+//   k_range       per parent node: the entry range of every binder edge in
+//                 the row / column of the bound end (a predicate-filtered
+//                 row selection, Eq. 15 / Eq. 19 / Eq. 23 for one node), and
+//                 the shortest of them;
+//   scan          exclusive offsets of the candidate counts;
+//   k_expand      load-balanced over all candidates: take the candidate from
+//                 the shortest range, keep it when it is in every other
+//                 binder range, passes the pre-pruning tests of Sec. 7.2.2
+//                 (candidate vector or predicate presence) and its
+//                 self-loops; survivors are appended with warp-aggregated
+//                 atomics.
+// A parent without candidates has no children, so dead bindings never
+// reach later levels (pre-pruning). Leaves (variables with one pattern)
+// are not materialized: k_enum_range stores their range per last-level
+// node and k_enum_write writes the cross product as int32 tuples.
+//
+// Workspace ("arena"): [control block | level 0 | level 1 | ... | output]
+// growing up, per-level scratch at the top growing down. Offsets are
+// functions of the level sizes, so every kernel recomputes them. A level or
+// an output that does not fit sets kStOverflow; the host then re-runs with
+// a larger arena.
+#include <algorithm>
+
+#include "gs_device.cuh"
+#include "gs_exec.h"
+
+namespace gs {
+
+__host__ __device__ __forceinline__ uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+__device__ __forceinline__ uint64_t level_off(const Ctl* c, int l) {
+    uint64_t o = kCtlBytes;
+    for (int j = 0; j < l; ++j) o += align256(8ull * c->n[j]);
+    return o;
+}
+
+// scratch for producing level l from np parent nodes with nbm binder slots
+__host__ __device__ __forceinline__ uint64_t scratch_bytes(uint64_t np, uint32_t nbm) {
+    return align256(8ull * np) + align256(8ull * np * nbm) + align256(np);
+}
+
+struct Scratch {
+    uint64_t* roff;
+    uint2* rng;
+    uint8_t* sel;
+    uint64_t base;
+};
+
+__device__ __forceinline__ Scratch scratch_at(const ExecDev& E, uint64_t np, uint32_t nbm) {
+    Scratch s;
+    uint64_t sb = scratch_bytes(np, nbm);
+    s.base = E.arena_bytes > sb ? E.arena_bytes - sb : 0;
+    s.roff = (uint64_t*)(E.arena + s.base);
+    s.rng = (uint2*)(E.arena + s.base + align256(8ull * np));
+    s.sel = (uint8_t*)(E.arena + s.base + align256(8ull * np) + align256(8ull * np * nbm));
+    return s;
+}
+
+__device__ __forceinline__ bool overflowed(const Ctl* c) {
+    return (*(volatile const uint32_t*)&c->status) & kStOverflow;
+}
+
+// Level base pointers in shared memory (computed once per block).
+__device__ __forceinline__ void load_levels(const ExecDev& E, int upto, const uint2** lv) {
+    if (threadIdx.x == 0) {
+        uint64_t o = kCtlBytes;
+        for (int j = 0; j <= upto && j < kMaxLevels; ++j) {
+            lv[j] = (const uint2*)(E.arena + o);
+            o += align256(8ull * E.ctl->n[j]);
+        }
+    }
+    __syncthreads();
+}
+
+// Bindings of levels 0..from of the node `idx` at level `from`.
+__device__ __forceinline__ void walk(const uint2* const* lv, int from, uint32_t idx, uint32_t* vid) {
+    for (int j = from; j >= 0; --j) {
+        uint2 e = lv[j][idx];
+        vid[j] = e.x;
+        idx = e.y;
+    }
+}
+
+__device__ __forceinline__ const DStore& store_of(const ExecDev& E, uint32_t dir) {
+    return dir == 0 ? E.out : E.in;
+}
+
+// ------------------------------------------------------------------ //
+
+__global__ void k_init(ExecDev E, ConstChecks cc) {
+    Ctl* c = E.ctl;
+    if (threadIdx.x == 0 && blockIdx.x == 0) c->one = 1;
+    for (uint32_t i = threadIdx.x; i < cc.n; i += blockDim.x) {
+        uint32_t s = cc.t[3 * i], p = cc.t[3 * i + 1], o = cc.t[3 * i + 2];
+        uint32_t lo, len;
+        label_range(E.out, s, p, lo, len);
+        if (!in_range(E.out, lo, len, o)) atomicOr(&c->dead, 1u);
+    }
+}
+
+// Candidate counts of the parent nodes of level l.
+__global__ void __launch_bounds__(kThreads) k_range(ExecDev E, int l, LevelSpec L) {
+    const Ctl* ctl = E.ctl;
+    if (overflowed(ctl)) return;
+    __shared__ const uint2* lv[kMaxLevels];
+    load_levels(E, l - 1, lv);
+    const uint64_t np = l == 0 ? 1 : ctl->n[l - 1];
+    const uint32_t nbm = L.n_binders > 0 ? L.n_binders : 1;
+    Scratch S = scratch_at(E, np, nbm);
+    if (S.base < level_off(ctl, l) + 256 || E.arena_bytes < scratch_bytes(np, nbm)) {
+        // the scratch would overlap the tree: report, write nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr((uint32_t*)&E.ctl->status, kStOverflow);
+        return;
+    }
+    const bool dead = ctl->dead != 0;
+    uint64_t beg, end;
+    block_chunk(np, blockIdx.x, gridDim.x, beg, end);
+    uint64_t sum = 0;
+    for (uint64_t i = beg + threadIdx.x; i < end; i += kThreads) {
+        uint64_t cnt = 0;
+        uint32_t sel = 0;
+        if (!dead) {
+            if (L.src == kSrcList) {
+                cnt = E.ctl->list_n[l];
+            } else {
+                uint32_t vid[kMaxLevels];
+                if (l > 0) walk(lv, l - 1, (uint32_t)i, vid);
+                uint32_t best = 0xffffffffu;
+                for (int b = 0; b < L.n_binders; ++b) {
+                    const Binder& B = L.b[b];
+                    uint32_t row = B.from_const ? B.c : vid[B.level];
+                    uint32_t lo, len;
+                    label_range(store_of(E, B.dir), row, B.label, lo, len);
+                    S.rng[i * nbm + b] = make_uint2(lo, len);
+                    if (len < best) { best = len; sel = (uint32_t)b; }
+                }
+                cnt = best;
+            }
+        }
+        S.roff[i] = cnt;
+        S.sel[i] = (uint8_t)sel;
+        sum += cnt;
+    }
+    sum = block_sum_u64(sum);
+    if (threadIdx.x == 0) E.ctl->bsum[blockIdx.x] = sum;
+}
+
+// Candidate test of the pre-pruning step and of the other binders.
+__device__ __forceinline__ bool keep_candidate(const ExecDev& E, const LevelSpec& L, int l,
+                                               uint32_t x, const uint2* rng, uint32_t sel) {
+    if (L.use_bitmap) {
+        const uint32_t* bm = E.bits + (uint64_t)l * E.words;
+        if (!((__ldg(bm + (x >> 5)) >> (x & 31)) & 1u)) return false;
+    }
+    for (int b = 0; b < L.n_binders; ++b) {
+        if ((uint32_t)b == sel) continue;
+        uint2 r = rng[b];
+        if (!in_range(store_of(E, L.b[b].dir), r.x, r.y, x)) return false;
+    }
+    for (int j = 0; j < L.n_probes; ++j)
+        if (!has_label(store_of(E, L.pr[j].dir), x, L.pr[j].label)) return false;
+    for (int j = 0; j < L.n_self; ++j) {
+        uint32_t lo, len;
+        label_range(E.out, x, L.self_label[j], lo, len);
+        if (!in_range(E.out, lo, len, x)) return false;
+    }
+    return true;
+}
+
+// Warp-aggregated append of (x, parent) to a level with capacity cap.
+__device__ __forceinline__ void append(Ctl* ctl, int l, uint2* dst, uint64_t cap, bool keep,
+                                       uint32_t x, uint32_t parent) {
+    const uint32_t lane = lane_id();
+    uint32_t m = __ballot_sync(0xffffffffu, keep);
+    if (!m) return;
+    uint64_t base = 0;
+    uint32_t leader = __ffs(m) - 1;
+    if (lane == leader) base = atomicAdd((unsigned long long*)&ctl->n[l], (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (keep) {
+        uint64_t pos = base + __popc(m & ((1u << lane) - 1u));
+        if (pos < cap) dst[pos] = make_uint2(x, parent);
+        else atomicOr(&ctl->status, kStOverflow);
+    }
+}
+
+constexpr int kExpItems = 8;                         // candidates per thread per tile
+constexpr uint64_t kExpTile = (uint64_t)kThreads * kExpItems;
+
+__device__ __forceinline__ uint64_t upper_bound_u64(const uint64_t* a, uint64_t lo, uint64_t hi,
+                                                    uint64_t key) {
+    while (lo < hi) {
+        uint64_t mid = lo + ((hi - lo) >> 1);
+        if (a[mid] <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec L) {
+    Ctl* ctl = E.ctl;
+    if (overflowed(ctl)) return;
+    __shared__ uint64_t tile_nodes[2];
+    const uint64_t np = l == 0 ? 1 : ctl->n[l - 1];
+    const uint32_t nbm = L.n_binders > 0 ? L.n_binders : 1;
+    Scratch S = scratch_at(E, np, nbm);
+    const uint64_t T = ctl->cand;
+    uint64_t base_l = kCtlBytes;
+    for (int j = 0; j < l; ++j) base_l += align256(8ull * ctl->n[j]);
+    const uint64_t cap = S.base > base_l ? (S.base - base_l) / 8 : 0;
+    uint2* dst = (uint2*)(E.arena + base_l);
+    const uint32_t* list = E.lists ? E.lists + (uint64_t)l * E.list_stride : nullptr;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * kExpTile; t0 < T; t0 += (uint64_t)gridDim.x * kExpTile) {
+        uint64_t t1 = min(t0 + kExpTile, T);
+        if (threadIdx.x == 0) {
+            tile_nodes[0] = upper_bound_u64(S.roff, 0, np, t0) - 1;
+            tile_nodes[1] = upper_bound_u64(S.roff, tile_nodes[0], np, t1 - 1);
+        }
+        __syncthreads();
+        const uint64_t i0 = tile_nodes[0], i1 = tile_nodes[1];
+        for (int k = 0; k < kExpItems; ++k) {
+            uint64_t q = t0 + (uint64_t)k * kThreads + threadIdx.x;
+            bool keep = false;
+            uint32_t x = 0, node = 0;
+            if (q < t1) {
+                uint64_t i = upper_bound_u64(S.roff, i0, i1, q) - 1;
+                node = (uint32_t)i;
+                uint64_t j = q - S.roff[i];
+                uint32_t sel = S.sel[i];
+                const uint2* rng = S.rng + i * nbm;
+                if (L.src == kSrcList) {
+                    x = list[j];
+                } else {
+                    uint2 r = rng[sel];
+                    x = __ldg(store_of(E, L.b[sel].dir).idx + r.x + j);
+                }
+                keep = keep_candidate(E, L, l, x, rng, L.src == kSrcList ? 0xffffffffu : sel);
+            }
+            append(ctl, l, dst, cap, keep, x, node);
+        }
+        __syncthreads();
+    }
+}
+
+// In-place exclusive scan of the candidate counts in the scratch of level l
+// (np = *np_ptr parents, nbm binder slots).
+__global__ void __launch_bounds__(kThreads) k_scan_apply_scratch(ExecDev E, const uint64_t* np_ptr,
+                                                                 uint32_t nbm) {
+    const Ctl* ctl = E.ctl;
+    if (overflowed(ctl) || (ctl->status & kStHuge)) return;
+    const uint64_t np = *np_ptr;
+    Scratch S = scratch_at(E, np, nbm);
+    uint64_t beg, end;
+    block_chunk(np, blockIdx.x, gridDim.x, beg, end);
+    uint64_t carry = ctl->boff[blockIdx.x];
+    for (uint64_t base = beg; base < end; base += kThreads) {
+        uint64_t i = base + threadIdx.x;
+        uint64_t v = i < end ? S.roff[i] : 0, t;
+        uint64_t ex = block_excl_scan_u64(v, &t);
+        if (i < end) S.roff[i] = carry + ex;
+        carry += t;
+    }
+}
+
+// ------------------------------------------------------------------ //
+// Candidate vector -> ordered vertex list (warp ballot / popc + block scan).
+
+__device__ __forceinline__ bool self_ok(const ExecDev& E, const LevelSpec& L, uint32_t x) {
+    for (int j = 0; j < L.n_self; ++j) {
+        uint32_t lo, len;
+        label_range(E.out, x, L.self_label[j], lo, len);
+        if (!in_range(E.out, lo, len, x)) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t word_keep(const ExecDev& E, const LevelSpec& L, uint32_t w,
+                                              uint32_t word) {
+    if (L.n_self == 0 || word == 0) return word;
+    uint32_t out = 0;
+    for (uint32_t m = word; m; m &= m - 1) {
+        uint32_t b = __ffs(m) - 1;
+        if (self_ok(E, L, w * 32 + b)) out |= 1u << b;
+    }
+    return out;
+}
+
+__global__ void __launch_bounds__(kThreads) k_bits_count(ExecDev E, int l, LevelSpec L) {
+    if (overflowed(E.ctl)) return;
+    const uint32_t* bm = E.bits + (uint64_t)l * E.words;
+    uint64_t beg, end;
+    block_chunk(E.words, blockIdx.x, gridDim.x, beg, end);
+    uint64_t c = 0;
+    if (!E.ctl->dead)
+        for (uint64_t w = beg + threadIdx.x; w < end; w += kThreads)
+            c += __popc(word_keep(E, L, (uint32_t)w, bm[w]));
+    c = block_sum_u64(c);
+    if (threadIdx.x == 0) E.ctl->bsum[blockIdx.x] = c;
+}
+
+// to_level: write (vertex, 0) pairs as level l (a root); else the list of level l
+__global__ void __launch_bounds__(kThreads) k_bits_write(ExecDev E, int l, LevelSpec L, int to_level) {
+    Ctl* ctl = E.ctl;
+    if (overflowed(ctl) || ctl->dead) return;
+    const uint32_t* bm = E.bits + (uint64_t)l * E.words;
+    uint64_t base_l = kCtlBytes;
+    for (int j = 0; j < l; ++j) base_l += align256(8ull * ctl->n[j]);
+    const uint64_t cap = E.arena_bytes > base_l ? (E.arena_bytes - base_l) / 8 : 0;
+    uint2* dst = (uint2*)(E.arena + base_l);
+    uint32_t* list = E.lists ? E.lists + (uint64_t)l * E.list_stride : nullptr;
+    uint64_t beg, end;
+    block_chunk(E.words, blockIdx.x, gridDim.x, beg, end);
+    uint64_t carry = ctl->boff[blockIdx.x];
+    for (uint64_t base = beg; base < end; base += kThreads) {
+        uint64_t w = base + threadIdx.x;
+        uint32_t word = w < end ? word_keep(E, L, (uint32_t)w, bm[w]) : 0u;
+        uint64_t t;
+        uint64_t pos = carry + block_excl_scan_u64(__popc(word), &t);
+        for (uint32_t m = word; m; m &= m - 1) {
+            uint32_t x = (uint32_t)w * 32 + (__ffs(m) - 1);
+            if (to_level) {
+                if (pos < cap) dst[pos] = make_uint2(x, 0u);
+                else atomicOr(&ctl->status, kStOverflow);
+            } else {
+                list[pos] = x;
+            }
+            ++pos;
+        }
+        carry += t;
+    }
+}
+
+// ------------------------------------------------------------------ //
+// Enumeration.
+
+constexpr uint64_t kCountCap = 1ull << 40;
+
+__global__ void __launch_bounds__(kThreads) k_enum_range(ExecDev E, int last, EnumSpec F) {
+    Ctl* ctl = E.ctl;
+    if (overflowed(ctl)) return;
+    __shared__ const uint2* lv[kMaxLevels];
+    load_levels(E, last, lv);
+    const uint64_t n = ctl->n[last];
+    const uint32_t nl = F.n_leaves > 0 ? F.n_leaves : 1;
+    Scratch S = scratch_at(E, n, nl);
+    if (S.base < level_off(ctl, last + 1) || E.arena_bytes < scratch_bytes(n, nl)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->status, kStOverflow);
+        return;
+    }
+    uint64_t beg, end;
+    block_chunk(n, blockIdx.x, gridDim.x, beg, end);
+    uint64_t sum = 0;
+    for (uint64_t i = beg + threadIdx.x; i < end; i += kThreads) {
+        uint64_t cnt = 1;
+        if (F.n_leaves > 0) {
+            uint32_t vid[kMaxLevels];
+            walk(lv, last, (uint32_t)i, vid);
+            for (int j = 0; j < F.n_leaves; ++j) {
+                const LeafSpec& Lf = F.leaf[j];
+                uint32_t lo, len;
+                label_range(store_of(E, Lf.dir), vid[Lf.level], Lf.label, lo, len);
+                S.rng[i * nl + j] = make_uint2(lo, len);
+                cnt = cnt * len;
+                if (cnt > kCountCap) { cnt = kCountCap; atomicOr(&ctl->status, kStHuge); }
+            }
+        }
+        S.roff[i] = cnt;
+        sum += cnt;
+    }
+    sum = block_sum_u64(sum);
+    if (threadIdx.x == 0) ctl->bsum[blockIdx.x] = sum;
+}
+
+__global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, EnumSpec F) {
+    Ctl* ctl = E.ctl;
+    if (overflowed(ctl) || (ctl->status & kStHuge)) return;
+    __shared__ const uint2* lv[kMaxLevels];
+    __shared__ uint64_t tile_nodes[2];
+    load_levels(E, last, lv);
+    const uint64_t n = ctl->n[last];
+    const uint32_t nl = F.n_leaves > 0 ? F.n_leaves : 1;
+    Scratch S = scratch_at(E, n, nl);
+    const uint64_t T = ctl->rows;
+    uint64_t out_off = kCtlBytes;
+    for (int j = 0; j <= last; ++j) out_off += align256(8ull * ctl->n[j]);
+    const uint64_t rowb = 4ull * F.n_vars;
+    const uint64_t cap = S.base > out_off ? (S.base - out_off) / rowb : 0;
+    if (T > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->status, kStOverflow);
+        return;
+    }
+    int32_t* out = (int32_t*)(E.arena + out_off);
+    for (uint64_t t0 = (uint64_t)blockIdx.x * kExpTile; t0 < T; t0 += (uint64_t)gridDim.x * kExpTile) {
+        uint64_t t1 = min(t0 + kExpTile, T);
+        if (threadIdx.x == 0) {
+            tile_nodes[0] = upper_bound_u64(S.roff, 0, n, t0) - 1;
+            tile_nodes[1] = upper_bound_u64(S.roff, tile_nodes[0], n, t1 - 1);
+        }
+        __syncthreads();
+        const uint64_t i0 = tile_nodes[0], i1 = tile_nodes[1];
+        for (int k = 0; k < kExpItems; ++k) {
+            uint64_t q = t0 + (uint64_t)k * kThreads + threadIdx.x;
+            if (q >= t1) continue;
+            uint64_t i = upper_bound_u64(S.roff, i0, i1, q) - 1;
+            uint64_t loc = q - S.roff[i];
+            uint32_t vid[kMaxLevels];
+            walk(lv, last, (uint32_t)i, vid);
+            uint32_t leafv[kMaxVars];
+            for (int j = F.n_leaves - 1; j >= 0; --j) {
+                uint2 r = S.rng[i * nl + j];
+                uint64_t d = loc % r.y;
+                loc /= r.y;
+                leafv[j] = __ldg(store_of(E, F.leaf[j].dir).idx + r.x + d);
+            }
+            int32_t* row = out + q * F.n_vars;
+            for (int v = 0; v < F.n_vars; ++v) {
+                int32_t src = F.var_src[v];
+                row[v] = (int32_t)(src >= 0 ? vid[src] : leafv[-src - 1]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ //
+
+uint64_t host_level_off(const uint64_t* n, int l) {
+    uint64_t o = kCtlBytes;
+    for (int j = 0; j < l; ++j) o += align256(8ull * n[j]);
+    return o;
+}
+
+gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
+                       cudaStream_t st) {
+    const int nb = g->n_blocks;
+    Ctl* ctl = E.ctl;
+    GS_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
+    ConstChecks cc{};
+    cc.n = (uint32_t)(P->const_triples.size() / 3);
+    if (cc.n > kMaxPatterns) cc.n = kMaxPatterns;
+    for (uint32_t i = 0; i < 3 * cc.n; ++i) cc.t[i] = P->const_triples[i];
+    k_init<<<1, kThreads, 0, st>>>(E, cc);
+    uint32_t nl_launch = 1;
+    if (P->needs_scan) {
+        gs_status rc = run_scan(g, P->scan, E.bits, scan_work, st);
+        if (rc != GS_OK) return rc;
+        nl_launch += 4;
+    }
+    for (int l = 0; l < P->n_levels; ++l) {
+        const LevelSpec& L = P->levels[l];
+        if (L.src == kSrcList) {
+            k_bits_count<<<nb, kThreads, 0, st>>>(E, l, L);
+            uint64_t* total = l == 0 ? &ctl->n[0] : &ctl->list_n[l];
+            k_scan_block_sums<<<1, kThreads, 0, st>>>(ctl->bsum, ctl->boff, nb, total, &ctl->status);
+            nl_launch += 3;
+            if (l == 0) {
+                k_bits_write<<<nb, kThreads, 0, st>>>(E, l, L, 1);
+                continue;
+            }
+            k_bits_write<<<nb, kThreads, 0, st>>>(E, l, L, 0);
+        }
+        nl_launch += 4;
+        const uint64_t* np_ptr = l == 0 ? &ctl->one : &ctl->n[l - 1];
+        const uint32_t nbm = L.n_binders > 0 ? L.n_binders : 1;
+        k_range<<<nb, kThreads, 0, st>>>(E, l, L);
+        k_scan_block_sums<<<1, kThreads, 0, st>>>(ctl->bsum, ctl->boff, nb, &ctl->cand, &ctl->status);
+        k_scan_apply_scratch<<<nb, kThreads, 0, st>>>(E, np_ptr, nbm);
+        k_expand<<<nb, kThreads, 0, st>>>(E, l, L);
+    }
+    const int last = P->n_levels - 1;
+    EnumSpec F{};
+    F.n_leaves = P->n_leaves;
+    F.n_vars = P->n_vars;
+    for (int j = 0; j < P->n_leaves; ++j) F.leaf[j] = P->leaves[j];
+    for (int v = 0; v < P->n_vars; ++v) F.var_src[v] = P->var_src[v];
+    const uint32_t nl = P->n_leaves > 0 ? P->n_leaves : 1;
+    k_enum_range<<<nb, kThreads, 0, st>>>(E, last, F);
+    k_scan_block_sums<<<1, kThreads, 0, st>>>(ctl->bsum, ctl->boff, nb, &ctl->rows, &ctl->status);
+    k_scan_apply_scratch<<<nb, kThreads, 0, st>>>(E, &ctl->n[last], nl);
+    k_enum_write<<<nb, kThreads, 0, st>>>(E, last, F);
+    nl_launch += 4;
+    if (launches) *launches = nl_launch;
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+}
+
+}  // namespace gs

@@ -1,0 +1,189 @@
+// Internal declarations of the engine: store, plan and executor structures
+// shared by the host code and the sm_103a kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gsmart.h"
+
+namespace gs {
+
+constexpr int kMaxVars = GS_MAX_VARS;        // 31: one bit per variable in 32-bit masks
+constexpr int kMaxPatterns = GS_MAX_PATTERNS;
+constexpr int kMaxLevels = 32;               // one materialized level per variable at most
+constexpr int kMaxBinders = 8;               // edges joining a level's variable to bound ends
+constexpr int kMaxProbes = 16;               // presence tests on a level's candidates
+constexpr int kMaxSelf = 8;                  // self-loop patterns ?w p ?w per variable
+constexpr int kMaxSlots = 31;                // distinct predicates per direction in one scan
+constexpr int kBlocks = 1024;                // upper bound of the fixed grid (blocks)
+constexpr int kThreads = 256;
+
+// Rows whose degree exceeds kHeavyDeg are scanned in chunks of kHeavyChunk
+// entries, one warp per chunk, instead of one lane per row.
+constexpr uint32_t kHeavyDeg = 64;
+constexpr uint32_t kHeavyChunk = 2048;
+
+// Status bits written by kernels into the control block.
+constexpr uint32_t kStOverflow = 1u;  // a level or the output did not fit the workspace
+constexpr uint32_t kStBadInput = 2u;
+
+const char* last_error();
+
+void set_error(const char* fmt, ...);
+gs_status cuda_fail(cudaError_t e, const char* what);
+
+#define GS_CUDA(call)                                            \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) return ::gs::cuda_fail(_e, #call); \
+    } while (0)
+
+// Device memory through the caller's hook or stream-ordered cudaMallocAsync.
+struct Alloc {
+    gs_allocator hook{};
+    bool has_hook = false;
+    void* get(size_t bytes, cudaStream_t st) const;
+    void put(void* p, cudaStream_t st) const;
+};
+
+// One orientation of the RDF matrix. Row r holds entries [ptr[r], ptr[r+1])
+// of idx (the other end) and lab (the predicate), sorted by (lab, idx).
+// idx and lab are padded with 4 zero words so aligned 16-byte loads that
+// start inside the array stay inside the allocation.
+struct Store {
+    uint32_t* ptr = nullptr;
+    uint32_t* idx = nullptr;
+    uint32_t* lab = nullptr;
+    // rows with more than kHeavyDeg entries, ascending, and their chunks
+    uint32_t* hrow = nullptr;       // [n_heavy]
+    uint32_t* chunk_h = nullptr;    // [n_chunks] index into hrow
+    uint32_t* chunk_start = nullptr;// [n_chunks] first entry of the chunk
+    uint32_t n_heavy = 0, n_chunks = 0;
+};
+
+// Device view passed to kernels by value.
+struct DStore {
+    const uint32_t* __restrict__ ptr;
+    const uint32_t* __restrict__ idx;
+    const uint32_t* __restrict__ lab;
+};
+
+inline DStore dview(const Store& s) { return DStore{s.ptr, s.idx, s.lab}; }
+
+}  // namespace gs
+
+struct gs_graph {
+    uint32_t N = 0, P = 0;
+    uint64_t M = 0;
+    gs::Store out;   // rows = subjects, idx = objects
+    gs::Store in;    // rows = objects,  idx = subjects
+    gs::Alloc alloc;
+    int sm_count = 148;
+    int n_blocks = 592;
+    int device = 0;
+};
+
+namespace gs {
+
+// An edge joining the variable w bound at a level to an end that is
+// already bound (a variable of an earlier level, or a constant vertex).
+struct Binder {
+    uint32_t label;
+    uint32_t c;          // constant vertex id when from_const
+    int16_t level;       // level of the bound variable when !from_const
+    uint8_t from_const;
+    uint8_t dir;         // 0: w is the object -> candidates in the CSR row of the bound end
+                         // 1: w is the subject -> candidates in the CSC column of the bound end
+};
+
+// Candidate x of a level must have predicate `label` in its row (dir 0)
+// or its column (dir 1): a pre-pruning test (Sec. 7.2.2) for edges whose
+// other end is bound later.
+struct Probe {
+    uint32_t label;
+    uint32_t dir;
+};
+
+enum : int32_t { kSrcBinders = 0, kSrcList = 1 };
+
+struct LevelSpec {
+    int32_t var;
+    int32_t src;           // kSrcBinders: candidates from the shortest binder range;
+                           // kSrcList: candidates = the variable's compacted candidate vector
+    int32_t n_binders;
+    int32_t n_probes;
+    int32_t n_self;
+    int32_t use_bitmap;    // test candidates against the variable's candidate vector
+    Binder b[kMaxBinders];
+    Probe pr[kMaxProbes];
+    uint32_t self_label[kMaxSelf];
+};
+
+// A variable with exactly one incident pattern whose other end is a
+// variable: never materialized, its bindings are the entries of one range
+// per tree node, expanded only when the tuples are written.
+struct LeafSpec {
+    int32_t var;
+    int32_t level;       // level of its only neighbour
+    uint32_t label;
+    uint32_t dir;        // as Binder::dir
+};
+
+struct ScanSpec {
+    int32_t n_out, n_in;               // distinct predicates tested on rows / columns
+    uint32_t out_pred[kMaxSlots];
+    uint32_t in_pred[kMaxSlots];
+    int32_t n_bvars;                   // candidate vectors produced
+    int32_t bvar[kMaxVars];            // which variable each vector belongs to
+    uint32_t need_out[kMaxVars];       // slot masks that must all be present
+    uint32_t need_in[kMaxVars];
+};
+
+}  // namespace gs
+
+struct gs_plan {
+    uint32_t N = 0, P = 0;
+    std::vector<int64_t> patterns;     // n x 3 as given
+    int n_vars = 0;
+    uint32_t flags = 0;
+    // planner output (Sec. 6.1): groups of (vertex, edge indices) and roots;
+    // vertex >= 0 is a variable, < 0 is -(1 + constant id)
+    std::vector<std::pair<int64_t, std::vector<int>>> groups;
+    std::vector<int64_t> roots;
+    // schedule for the executor
+    int n_levels = 0;
+    gs::LevelSpec levels[gs::kMaxLevels];
+    int n_leaves = 0;
+    gs::LeafSpec leaves[gs::kMaxVars];
+    int32_t var_src[gs::kMaxVars];    // >= 0: level of the variable; < 0: -(leaf + 1)
+    bool needs_scan = false;
+    gs::ScanSpec scan{};
+    std::vector<uint32_t> const_triples;   // patterns with two constant ends: s, p, o
+};
+
+namespace gs {
+
+// store.cu
+gs_status build_store(gs_graph* g, const uint32_t* s, const uint32_t* p, const uint32_t* o,
+                      uint64_t n, bool on_device, cudaStream_t st);
+void free_store(gs_graph* g, cudaStream_t st);
+// radix sort of 64-bit keys on bits [lo_bit, hi_bit); keys end up in *keys
+// (the buffers may be swapped). tmp must hold n keys.
+gs_status radix_sort_u64(const gs_graph* g, uint64_t** keys, uint64_t** tmp, uint64_t n,
+                         int lo_bit, int hi_bit, cudaStream_t st);
+
+// scan.cu: candidate vectors (Eq. 17 / Eq. 21) of the variables in spec.
+// bits: spec.n_bvars vectors of ceil(N/32) words. work: scan_work_bytes().
+size_t scan_work_bytes(const gs_graph* g);
+gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void* work,
+                   cudaStream_t st);
+
+// plan.cpp
+gs_status make_plan(const gs_graph* g, const int64_t* patterns, uint32_t n, uint32_t flags,
+                    gs_plan** out);
+
+}  // namespace gs

@@ -1,0 +1,393 @@
+// Query planner (Sec. 6.1) and the schedule the executor runs.
+//
+// The planner builds the query graph (one vertex per variable and per
+// distinct constant, one edge per triple pattern) and orders the edges in
+// groups: the degree-driven traversal of Sec. 6.1.2 (with its constant
+// variant) or the direction-driven traversal of Sec. 6.1.1 (with its cyclic
+// variant). Where the text leaves a choice open the planner takes these
+// readings: the root joins the visited set W when chosen; only vertices new
+// to W are pushed; remaining ties go to the lower vertex (variables before
+// constants, then by index), which wins a root choice and is pushed last so
+// it is popped first; a popped vertex without unevaluated edges yields no
+// group; with constants, when no unvisited vertex next to a constant is
+// left, the root is chosen by the rule without constants.
+//
+// Schedule. Variables are materialized in the order the groups reach them
+// (a group's own vertex, then the new ends of its edges): one tree level
+// per variable (Sec. 7.1, one path through all groups). A variable's
+// "binders" are its patterns to constants and to variables of earlier
+// levels; each tree node takes its candidates from the shortest binder
+// range and tests the others by membership. Its patterns to variables of
+// later levels become pre-pruning tests (Sec. 7.2.2): presence of the
+// predicate in the candidate's row / column, or the candidate vector of
+// the triple scan (Eq. 17 / Eq. 21) when one was computed. A variable with
+// a single pattern to another variable is not materialized (a leaf).
+#include <algorithm>
+#include <cstring>
+#include <set>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+struct QVert {
+    bool is_const;
+    int64_t id;   // variable index or constant vertex id
+    bool operator<(const QVert& o) const {
+        if (is_const != o.is_const) return !is_const;   // variables first
+        return id < o.id;
+    }
+    bool operator==(const QVert& o) const { return is_const == o.is_const && id == o.id; }
+    int64_t code() const { return is_const ? -(1 + id) : id; }
+};
+
+struct QGraph {
+    std::vector<QVert> V;                       // sorted
+    std::vector<std::pair<int, int>> E;         // (subject vertex, object vertex) indices into V
+};
+
+int vindex(const QGraph& G, const QVert& v) {
+    return (int)(std::lower_bound(G.V.begin(), G.V.end(), v) - G.V.begin());
+}
+
+QGraph make_graph(const int64_t* pat, uint32_t n) {
+    QGraph G;
+    std::set<QVert> vs;
+    auto vk = [](int64_t x) { return x < 0 ? QVert{false, -x - 1} : QVert{true, x}; };
+    for (uint32_t i = 0; i < n; ++i) { vs.insert(vk(pat[3 * i])); vs.insert(vk(pat[3 * i + 2])); }
+    G.V.assign(vs.begin(), vs.end());
+    for (uint32_t i = 0; i < n; ++i)
+        G.E.push_back({vindex(G, vk(pat[3 * i])), vindex(G, vk(pat[3 * i + 2]))});
+    return G;
+}
+
+struct Trav {
+    const QGraph& G;
+    std::vector<char> F;   // evaluated edges
+    explicit Trav(const QGraph& g) : G(g), F(g.E.size(), 0) {}
+    int n_out(int v) const { int c = 0; for (size_t i = 0; i < G.E.size(); ++i) c += !F[i] && G.E[i].first == v; return c; }
+    int n_in(int v) const { int c = 0; for (size_t i = 0; i < G.E.size(); ++i) c += !F[i] && G.E[i].second == v; return c; }
+    int n_inc(int v) const { int c = 0; for (size_t i = 0; i < G.E.size(); ++i) c += !F[i] && (G.E[i].first == v || G.E[i].second == v); return c; }
+    bool all_done() const { for (char f : F) if (!f) return false; return true; }
+};
+
+using Groups = std::vector<std::pair<int, std::vector<int>>>;
+
+// Sec. 6.1.2
+void degree_driven(const QGraph& G, Groups& groups, std::vector<int>& roots) {
+    Trav T(G);
+    const int nv = (int)G.V.size();
+    std::vector<char> W(nv, 0);
+    bool has_const = false;
+    for (int v = 0; v < nv; ++v) if (G.V[v].is_const) { W[v] = 1; has_const = true; }
+    if (has_const) {   // constant variant of step 1: evaluate all edges of the constants
+        for (int c = 0; c < nv; ++c) {
+            if (!G.V[c].is_const) continue;
+            std::vector<int> es;
+            for (size_t i = 0; i < G.E.size(); ++i)
+                if (!T.F[i] && (G.E[i].first == c || G.E[i].second == c)) es.push_back((int)i);
+            if (es.empty()) continue;
+            for (int i : es) T.F[i] = 1;
+            groups.push_back({c, es});
+        }
+    }
+    while (!T.all_done()) {
+        std::vector<int> cand;
+        for (int v = 0; v < nv; ++v) if (!W[v]) cand.push_back(v);
+        if (has_const) {   // constant variant of step 2: next to a constant
+            std::vector<int> adj;
+            for (int v : cand) {
+                bool a = false;
+                for (auto& e : G.E)
+                    if ((e.first == v && G.V[e.second].is_const) || (e.second == v && G.V[e.first].is_const)) a = true;
+                if (a) adj.push_back(v);
+            }
+            if (!adj.empty()) cand = adj;
+        }
+        int root = -1, bi = -1, bo = -1;
+        for (int v : cand) {   // cand is ascending, so strict '>' keeps the lower vertex on ties
+            int ni = T.n_inc(v), no = T.n_out(v);
+            if (root < 0 || ni > bi || (ni == bi && no > bo)) { root = v; bi = ni; bo = no; }
+        }
+        roots.push_back(root);
+        W[root] = 1;
+        std::vector<int> S{root};
+        while (!S.empty()) {
+            int v = S.back();
+            S.pop_back();
+            std::vector<int> es;
+            for (size_t i = 0; i < G.E.size(); ++i)
+                if (!T.F[i] && (G.E[i].first == v || G.E[i].second == v)) es.push_back((int)i);
+            if (es.empty()) continue;
+            for (int i : es) T.F[i] = 1;
+            groups.push_back({v, es});
+            std::vector<int> nw;
+            for (int i : es) {
+                int w = G.E[i].first == v ? G.E[i].second : G.E[i].first;
+                if (!W[w] && std::find(nw.begin(), nw.end(), w) == nw.end()) nw.push_back(w);
+            }
+            for (int w : nw) W[w] = 1;
+            // ascending by (unevaluated edges, unevaluated out-edges), lower vertex last
+            std::stable_sort(nw.begin(), nw.end(), [&](int a, int b) {
+                int ia = T.n_inc(a), ib = T.n_inc(b);
+                if (ia != ib) return ia < ib;
+                int oa = T.n_out(a), ob = T.n_out(b);
+                if (oa != ob) return oa < ob;
+                return a > b;
+            });
+            for (int w : nw) S.push_back(w);
+        }
+    }
+}
+
+// Sec. 6.1.1
+void direction_driven(const QGraph& G, Groups& groups, std::vector<int>& roots) {
+    Trav T(G);
+    const int nv = (int)G.V.size();
+    std::vector<char> W(nv, 0);
+    while (!T.all_done()) {
+        int root = -1, bo = -1;
+        for (int pass = 0; pass < 2 && root < 0; ++pass) {   // pass 1: cyclic variant
+            for (int v = 0; v < nv; ++v) {
+                if (W[v]) continue;
+                if (pass == 0 && T.n_in(v) > 0) continue;
+                int no = T.n_out(v);
+                if (root < 0 || no > bo) { root = v; bo = no; }
+            }
+        }
+        roots.push_back(root);
+        W[root] = 1;
+        std::vector<int> S{root};
+        while (!S.empty()) {
+            int v = S.back();
+            S.pop_back();
+            std::vector<int> es;
+            for (size_t i = 0; i < G.E.size(); ++i)
+                if (!T.F[i] && G.E[i].first == v) es.push_back((int)i);
+            if (es.empty()) continue;
+            for (int i : es) T.F[i] = 1;
+            groups.push_back({v, es});
+            std::vector<int> nw;
+            for (int i : es) {
+                int w = G.E[i].second;
+                if (!W[w] && std::find(nw.begin(), nw.end(), w) == nw.end()) nw.push_back(w);
+            }
+            for (int w : nw) W[w] = 1;
+            std::stable_sort(nw.begin(), nw.end(), [&](int a, int b) {
+                int oa = T.n_out(a), ob = T.n_out(b);
+                if (oa != ob) return oa < ob;
+                return a > b;
+            });
+            for (int w : nw) S.push_back(w);
+        }
+    }
+}
+
+}  // namespace
+
+gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t flags,
+                    gs_plan** out) {
+    *out = nullptr;
+    if (!pat || n == 0 || n > (uint32_t)kMaxPatterns) {
+        set_error("gs_plan_query: need 1..%d patterns", kMaxPatterns);
+        return GS_EINVAL;
+    }
+    if (flags > GS_PLAN_DIRECTION) { set_error("gs_plan_query: unknown flags %u", flags); return GS_EINVAL; }
+    const uint32_t N = g ? g->N : 0xffffffffu, NP = g ? g->P : 65535u;
+    int k = 0;
+    std::vector<char> used(kMaxVars + 1, 0);
+    for (uint32_t i = 0; i < n; ++i) {
+        int64_t p = pat[3 * i + 1];
+        if (p < 1 || p > (int64_t)NP) { set_error("gs_plan_query: pattern %u predicate %lld outside 1..%u", i, (long long)p, NP); return GS_EINVAL; }
+        for (int j : {0, 2}) {
+            int64_t x = pat[3 * i + j];
+            if (x >= 0) {
+                if (x >= (int64_t)N || x >= (1ll << 31)) { set_error("gs_plan_query: pattern %u vertex %lld out of range", i, (long long)x); return GS_EINVAL; }
+            } else {
+                int64_t v = -x - 1;
+                if (v >= kMaxVars) { set_error("gs_plan_query: at most %d variables", kMaxVars); return GS_EINVAL; }
+                used[v] = 1;
+                k = std::max<int>(k, (int)v + 1);
+            }
+        }
+    }
+    if (k == 0) { set_error("gs_plan_query: the query has no variable"); return GS_EINVAL; }
+    for (int v = 0; v < k; ++v)
+        if (!used[v]) { set_error("gs_plan_query: variables must be numbered 0..K-1 (variable %d unused)", v); return GS_EINVAL; }
+
+    gs_plan* P = new gs_plan();
+    P->N = g ? g->N : 0; P->P = g ? g->P : 0; P->flags = flags; P->n_vars = k;
+    P->patterns.assign(pat, pat + 3 * (size_t)n);
+
+    QGraph G = make_graph(pat, n);
+    Groups groups;
+    std::vector<int> roots;
+    bool has_const = false;
+    for (auto& v : G.V) has_const |= v.is_const;
+    if (flags == GS_PLAN_DIRECTION && !has_const) direction_driven(G, groups, roots);
+    else degree_driven(G, groups, roots);
+    for (auto& gr : groups) P->groups.push_back({G.V[gr.first].code(), gr.second});
+    for (int r : roots) P->roots.push_back(G.V[r].code());
+
+    // ---- schedule ----
+    auto var_of = [&](int64_t x) { return x < 0 ? (int)(-x - 1) : -1; };
+    std::vector<int> deg(k, 0);
+    std::vector<char> is_root(k, 0);
+    for (int r : roots) if (!G.V[r].is_const) is_root[G.V[r].id] = 1;
+    for (uint32_t i = 0; i < n; ++i) {
+        int a = var_of(pat[3 * i]), b = var_of(pat[3 * i + 2]);
+        if (a >= 0) deg[a]++;
+        if (b >= 0 && b != a) deg[b]++;
+        if (a >= 0 && a == b) deg[a]++;   // a self-loop is never a leaf edge
+    }
+    std::vector<int> leaf_pat(k, -1);
+    for (int v = 0; v < k; ++v) {
+        if (deg[v] != 1 || is_root[v]) continue;
+        for (uint32_t i = 0; i < n; ++i) {
+            int a = var_of(pat[3 * i]), b = var_of(pat[3 * i + 2]);
+            if ((a == v && b >= 0 && b != v) || (b == v && a >= 0 && a != v)) leaf_pat[v] = (int)i;
+        }
+    }
+    // two leaves joined by one pattern cannot both stay leaves
+    for (int v = 0; v < k; ++v) {
+        if (leaf_pat[v] < 0) continue;
+        int i = leaf_pat[v];
+        int a = var_of(pat[3 * i]), b = var_of(pat[3 * i + 2]);
+        int w = a == v ? b : a;
+        if (leaf_pat[w] >= 0) leaf_pat[std::max(v, w)] = -1;
+    }
+    std::vector<int> level_of(k, -1), order;
+    auto materialize = [&](int v) {
+        if (v < 0 || level_of[v] >= 0 || leaf_pat[v] >= 0) return;
+        level_of[v] = (int)order.size();
+        order.push_back(v);
+    };
+    for (auto& gr : groups) {
+        const QVert& gv = G.V[gr.first];
+        if (!gv.is_const) materialize((int)gv.id);
+        for (int e : gr.second) {
+            int a = G.E[e].first, b = G.E[e].second;
+            int w = a == gr.first ? b : a;
+            if (!G.V[w].is_const) materialize((int)G.V[w].id);
+        }
+    }
+    for (int v = 0; v < k; ++v) materialize(v);   // not reached by any group (cannot happen)
+    P->n_levels = (int)order.size();
+    bool need_scan = false, too_many_probes = false;
+    for (int l = 0; l < P->n_levels; ++l) {
+        LevelSpec& L = P->levels[l];
+        std::memset(&L, 0, sizeof(L));
+        int w = order[l];
+        L.var = w;
+        for (uint32_t i = 0; i < n; ++i) {
+            int64_t s = pat[3 * i], o = pat[3 * i + 2];
+            uint32_t p = (uint32_t)pat[3 * i + 1];
+            int a = var_of(s), b = var_of(o);
+            if (a == w && b == w) {
+                bool dup = false;   // a repeated pattern adds no constraint
+                for (int j = 0; j < L.n_self; ++j) dup |= L.self_label[j] == p;
+                if (dup) continue;
+                if (L.n_self >= kMaxSelf) { delete P; set_error("gs_plan_query: more than %d self-loop patterns on one variable", kMaxSelf); return GS_ENOTIMPL; }
+                L.self_label[L.n_self++] = p;
+                continue;
+            }
+            if (a != w && b != w) continue;
+            bool w_is_subject = a == w;
+            int other = w_is_subject ? b : a;
+            int64_t other_const = w_is_subject ? o : s;
+            bool bound = other < 0 || level_of[other] >= 0 && level_of[other] < l;
+            if (bound) {
+                bool dup = false;
+                for (int j = 0; j < L.n_binders; ++j) {
+                    const Binder& B = L.b[j];
+                    dup |= B.label == p && B.dir == (w_is_subject ? 1 : 0) &&
+                           (other < 0 ? (B.from_const && B.c == (uint32_t)other_const)
+                                      : (!B.from_const && B.level == level_of[other]));
+                }
+                if (dup) continue;
+                if (L.n_binders >= kMaxBinders) { delete P; set_error("gs_plan_query: more than %d edges join one variable to bound ends", kMaxBinders); return GS_ENOTIMPL; }
+                Binder& B = L.b[L.n_binders++];
+                B.label = p;
+                B.from_const = other < 0;
+                B.c = other < 0 ? (uint32_t)other_const : 0;
+                B.level = other < 0 ? -1 : (int16_t)level_of[other];
+                B.dir = w_is_subject ? 1 : 0;
+            } else {
+                bool dup = false;
+                for (int j = 0; j < L.n_probes; ++j)
+                    dup |= L.pr[j].label == p && L.pr[j].dir == (w_is_subject ? 0u : 1u);
+                if (dup) continue;
+                if (L.n_probes >= kMaxProbes) { too_many_probes = true; continue; }
+                L.pr[L.n_probes].label = p;
+                L.pr[L.n_probes].dir = w_is_subject ? 0 : 1;
+                L.n_probes++;
+            }
+        }
+        L.src = L.n_binders > 0 ? kSrcBinders : kSrcList;
+        if (L.src == kSrcList) need_scan = true;
+    }
+    if (too_many_probes) need_scan = true;
+    for (int v = 0; v < k; ++v) P->var_src[v] = level_of[v];
+    P->n_leaves = 0;
+    for (int v = 0; v < k; ++v) {
+        if (leaf_pat[v] < 0) continue;
+        int i = leaf_pat[v];
+        int a = var_of(pat[3 * i]), b = var_of(pat[3 * i + 2]);
+        LeafSpec& F = P->leaves[P->n_leaves];
+        F.var = v;
+        F.label = (uint32_t)pat[3 * i + 1];
+        int anchor = a == v ? b : a;
+        F.level = level_of[anchor];
+        F.dir = (b == v) ? 0 : 1;     // leaf is the object -> CSR row of the anchor
+        P->var_src[v] = -(P->n_leaves + 1);
+        P->n_leaves++;
+    }
+    for (uint32_t i = 0; i < n; ++i)
+        if (pat[3 * i] >= 0 && pat[3 * i + 2] >= 0) {
+            P->const_triples.push_back((uint32_t)pat[3 * i]);
+            P->const_triples.push_back((uint32_t)pat[3 * i + 1]);
+            P->const_triples.push_back((uint32_t)pat[3 * i + 2]);
+        }
+
+    P->needs_scan = need_scan;
+    if (need_scan) {
+        // candidate vectors of every materialized variable over all its patterns
+        ScanSpec& S = P->scan;
+        std::memset(&S, 0, sizeof(S));
+        auto slot = [&](uint32_t* preds, int32_t& cnt, uint32_t p) -> int {
+            for (int j = 0; j < cnt; ++j) if (preds[j] == p) return j;
+            if (cnt >= kMaxSlots) return -1;
+            preds[cnt] = p;
+            return cnt++;
+        };
+        for (int l = 0; l < P->n_levels; ++l) {
+            int w = order[l];
+            int bi = S.n_bvars++;
+            S.bvar[bi] = w;
+            for (uint32_t i = 0; i < n; ++i) {
+                int a = var_of(pat[3 * i]), b = var_of(pat[3 * i + 2]);
+                uint32_t p = (uint32_t)pat[3 * i + 1];
+                if (a == w) {
+                    int s = slot(S.out_pred, S.n_out, p);
+                    if (s < 0) { delete P; set_error("gs_plan_query: more than %d distinct out-predicates", kMaxSlots); return GS_ENOTIMPL; }
+                    S.need_out[bi] |= 1u << s;
+                }
+                if (b == w) {
+                    int s = slot(S.in_pred, S.n_in, p);
+                    if (s < 0) { delete P; set_error("gs_plan_query: more than %d distinct in-predicates", kMaxSlots); return GS_ENOTIMPL; }
+                    S.need_in[bi] |= 1u << s;
+                }
+            }
+        }
+        for (int l = 0; l < P->n_levels; ++l) {
+            P->levels[l].use_bitmap = 1;
+            P->levels[l].n_probes = 0;
+        }
+    }
+    *out = P;
+    return GS_OK;
+}
+
+}  // namespace gs

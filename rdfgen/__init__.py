@@ -179,7 +179,7 @@ class Sampler:
                                            _ptr(pat), _ptr(usub))
         return Query(pat, shape.n_v - len(shape.const), shape.name, bound, mapped)
 
-    def sample(self, shape: Shape, seed: int, qid: int, cap: float, tries: int = 6,
+    def sample(self, shape: Shape, seed: int, qid: int, cap: float, tries: int = 3,
                escalate: bool = True):
         """First embedding of `shape` whose spanning-tree bound is <= cap.
 

@@ -329,12 +329,36 @@ double rdfgen_tree_bound(const rdf_adj* g, uint32_t n_sv, const uint32_t* se,
                 }
             }
         } else {
-            for (uint64_t t = g->pred_off[p]; t < g->pred_off[p + 1]; ++t) {
-                uint64_t ti = g->pred_idx[t];
-                uint32_t x = us ? g->s[ti] : g->o[ti];
-                uint32_t y = us ? g->o[ti] : g->s[ti];
-                tmp[x] += f[w][y];
+            /* per-thread partial sums, then a reduction over x */
+            int nt = 1;
+#ifdef _OPENMP
+            nt = omp_get_max_threads();
+#endif
+            double* part = (double*)calloc((size_t)nt * N, sizeof(double));
+            const uint64_t b0 = g->pred_off[p], b1 = g->pred_off[p + 1];
+            const double* fw = f[w];
+            #pragma omp parallel num_threads(nt)
+            {
+                int tid = 0;
+#ifdef _OPENMP
+                tid = omp_get_thread_num();
+#endif
+                double* mine = part + (size_t)tid * N;
+                #pragma omp for schedule(static)
+                for (int64_t t = (int64_t)b0; t < (int64_t)b1; ++t) {
+                    uint64_t ti = g->pred_idx[t];
+                    uint32_t x = us ? g->s[ti] : g->o[ti];
+                    uint32_t y = us ? g->o[ti] : g->s[ti];
+                    mine[x] += fw[y];
+                }
+                #pragma omp for schedule(static)
+                for (int64_t x = 0; x < (int64_t)N; ++x) {
+                    double acc = 0.0;
+                    for (int k = 0; k < nt; ++k) acc += part[(size_t)k * N + x];
+                    tmp[x] = acc;
+                }
             }
+            free(part);
         }
         uint64_t nz = 0;
         for (uint32_t x = 0; x < N; ++x) { f[u][x] *= tmp[x]; nz += f[u][x] != 0.0; }

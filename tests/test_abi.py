@@ -1,0 +1,109 @@
+"""The C ABI without a GPU: the library loads, exports every entry point the
+header declares, plans queries (host only) like the oracle planner, and
+rejects bad input with a status instead of crashing. CPU only."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2106_14038_b300 as gs
+from oracle import planner as oplanner
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gsmart.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(gs_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_entry_point():
+    lib = gs.load_library()
+    names = _declared()
+    assert "gs_eval_query" in names and "gs_load_triples" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(gs.EXPORTED) == sorted(n for n in names)
+
+
+def test_load_without_gpu_reports_cuda_status():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = gs.load_library()
+    s = np.zeros(1, np.uint32)
+    h = ctypes.c_void_p()
+    rc = lib.gs_load_triples(s.ctypes.data_as(ctypes.c_void_p), s.ctypes.data_as(ctypes.c_void_p),
+                             s.ctypes.data_as(ctypes.c_void_p), 1, 4, 2, 0, None, None,
+                             ctypes.byref(h))
+    assert rc == 3  # GS_ECUDA
+    assert lib.gs_last_error()
+
+
+def _plan_nograph(pat, flags=0):
+    lib = gs.load_library()
+    pat = np.ascontiguousarray(np.asarray(pat, np.int64).reshape(-1, 3))
+    h = ctypes.c_void_p()
+    rc = lib.gs_plan_query(None, pat.ctypes.data_as(ctypes.c_void_p), len(pat), flags,
+                           ctypes.byref(h))
+    if rc != 0:
+        return rc, None
+    p = gs.Plan.__new__(gs.Plan)
+    p._h = h
+    p.patterns = pat
+    return 0, p
+
+
+def _oracle_fmt(groups, roots):
+    def v(x):
+        return x[1] if x[0] == "v" else ("c", x[1])
+    return [(v(g), list(es)) for g, es in groups], [v(r) for r in roots]
+
+
+@pytest.mark.parametrize("flags,fn", [(0, oplanner.degree_driven), (1, oplanner.direction_driven)])
+def test_planner_matches_oracle_planner(flags, fn):
+    rng = np.random.default_rng(11 + flags)
+    for _ in range(400):
+        k = int(rng.integers(1, 8))
+        n = int(rng.integers(1, 10))
+        pats = []
+        for _ in range(n):
+            ends = []
+            for _ in range(2):
+                if rng.random() < 0.15:
+                    ends.append(int(rng.integers(0, 20)))
+                else:
+                    ends.append(-int(rng.integers(0, k)) - 1)
+            pats.append((ends[0], int(rng.integers(1, 5)), ends[1]))
+        used = sorted({-x - 1 for t in pats for x in (t[0], t[2]) if x < 0})
+        if not used:
+            continue
+        remap = {v: i for i, v in enumerate(used)}
+        pats = [(-(remap[-a - 1]) - 1 if a < 0 else a, p, -(remap[-b - 1]) - 1 if b < 0 else b)
+                for a, p, b in pats]
+        rc, plan = _plan_nograph(pats, flags)
+        assert rc == 0
+        want = _oracle_fmt(*fn(pats))
+        assert plan.describe() == want, pats
+
+
+def test_planner_examples_6_1_and_6_2():
+    pats = [(-1, 1, -2), (-1, 2, -3), (-3, 3, -2), (-4, 4, -3)]   # Fig. 2b
+    _, p = _plan_nograph(pats, 1)
+    assert p.describe() == ([(0, [0, 1]), (2, [2]), (3, [3])], [0, 3])
+    _, p = _plan_nograph(pats, 0)
+    assert p.describe() == ([(2, [1, 2, 3]), (0, [0])], [2])
+
+
+@pytest.mark.parametrize("pat", [
+    [(0, 1, 1)],                 # no variable
+    [(-1, 0, -2)],               # predicate 0
+    [(-1, 1, -3)],               # variables not dense
+    [(-1, 70000, -2)],           # predicate beyond the largest id
+    [(-1, 1, -2)] * 33,          # too many patterns
+])
+def test_planner_rejects_bad_queries(pat):
+    rc, _ = _plan_nograph(pat)
+    assert rc == 1  # GS_EINVAL

@@ -1,0 +1,246 @@
+"""CUDA path against the oracle, element by element, through the C ABI.
+
+Every comparison is exact (integer ids): the store's arrays, the candidate
+vectors of the triple scan (Eq. 17 / Eq. 21) and the sorted answer rows."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2106_14038_b300 as gs
+import rdfgen
+
+pytestmark = pytest.mark.gpu
+
+
+def _graph(s, p, o, nv, npred):
+    return gs.Graph(s, p, o, nv, npred), oracle.Index(s, p, o, nv, npred)
+
+
+def _bits_to_bool(words, n):
+    w = np.asarray(words.cpu().numpy(), np.int64) & 0xffffffff
+    b = ((w[:, None] >> np.arange(32)) & 1).astype(bool).reshape(-1)
+    return b[:n]
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    w = rdfgen.WORKLOADS["rmat14"]
+    s, p, o = rdfgen.graph(w)
+    g, ix = _graph(s, p, o, w.n_vertices, w.n_preds)
+    return w, (s, p, o), g, ix
+
+
+def test_store_matches_oracle(rmat14):
+    w, _, g, ix = rmat14
+    assert g.n_triples == len(ix)
+    for by_col in (0, 1):
+        ts, tp, to = ix.triples(by_object=bool(by_col))
+        rows, other = (to, ts) if by_col else (ts, to)
+        ptr, idx, lab = oracle.csr_arrays(rows, tp, other, w.n_vertices)
+        gp, gi, gl = g.export(by_column=bool(by_col))
+        assert np.array_equal(gp.astype(np.int64), ptr)
+        assert np.array_equal(gi, idx)
+        assert np.array_equal(gl, lab)
+
+
+def test_store_example_6_3(golden):
+    g = {k: [int(x) for x in v.split()] for k, v in golden("ex63_csr.txt")}
+    rows = [i for i in range(8) if g["Mr"][i + 1] - g["Mr"][i] == 1]
+    s, p, o = [], [], []
+    for r, i in enumerate(rows):
+        for k in range(g["Pr"][r], g["Pr"][r + 1]):
+            s.append(i); p.append(g["Val"][k]); o.append(g["Col"][k])
+    G = gs.Graph(np.array(s), np.array(p), np.array(o), 8, 3)
+    ptr, idx, lab = G.export()
+    nonempty = np.diff(ptr.astype(np.int64)) > 0
+    assert np.concatenate([[0], np.cumsum(nonempty)]).tolist() == g["Mr"]
+    assert np.concatenate([[0], np.cumsum(np.diff(ptr.astype(np.int64))[nonempty])]).tolist() == g["Pr"]
+    for r, i in enumerate(np.nonzero(nonempty)[0]):
+        want = sorted(zip(g["Val"][g["Pr"][r]:g["Pr"][r + 1]], g["Col"][g["Pr"][r]:g["Pr"][r + 1]]))
+        got = list(zip(lab[ptr[i]:ptr[i + 1]].tolist(), idx[ptr[i]:ptr[i + 1]].tolist()))
+        assert got == want      # sorted by (label, column) inside the row
+
+
+def test_store_rejects_bad_triples():
+    s = np.array([0, 5], np.uint32)
+    p = np.array([1, 1], np.uint32)
+    o = np.array([1, 1], np.uint32)
+    with pytest.raises(gs.GsError) as e:
+        gs.Graph(s, p, o, 4, 2)
+    assert e.value.status == 1
+    with pytest.raises(gs.GsError):
+        gs.Graph(s[:1], np.array([3], np.uint32), o[:1], 4, 2)
+
+
+def test_store_device_input_and_duplicates():
+    import torch
+    s = torch.tensor([0, 0, 1, 1, 1, 2], dtype=torch.int32, device="cuda")
+    p = torch.tensor([1, 1, 2, 1, 2, 1], dtype=torch.int32, device="cuda")
+    o = torch.tensor([1, 1, 2, 0, 2, 2], dtype=torch.int32, device="cuda")
+    g = gs.Graph(s, p, o, 3, 2)
+    assert g.n_triples == 4
+    ptr, idx, lab = g.export()
+    assert ptr.tolist() == [0, 1, 3, 4]
+    assert list(zip(lab.tolist(), idx.tolist())) == [(1, 1), (1, 0), (2, 2), (1, 2)]
+
+
+def _scan_cases(npred, rng, n_cases):
+    for _ in range(n_cases):
+        m = int(rng.integers(1, 5))
+        preds = rng.integers(1, npred + 1, m)
+        dirs = rng.integers(0, 2, m)
+        yield preds, dirs
+
+
+def test_scan_matches_oracle(rmat14):
+    w, _, g, ix = rmat14
+    rng = np.random.default_rng(3)
+    pres = {}
+    for preds, dirs in _scan_cases(w.n_preds, rng, 40):
+        want = np.ones(w.n_vertices, bool)
+        for q, d in zip(preds, dirs):
+            key = (int(d), int(q))
+            if key not in pres:
+                pres[key] = ix.presence(int(d), int(q)).astype(bool)
+            want &= pres[key]
+        got = _bits_to_bool(g.scan(preds, dirs), w.n_vertices)
+        assert np.array_equal(got, want), (preds, dirs)
+
+
+def test_scan_heavy_rows_and_ragged_tail():
+    # vertex 7 has 9000 out- and 7000 in-edges (several scan chunks), and N is
+    # not a multiple of 32 so the last word is partial
+    rng = np.random.default_rng(5)
+    n_v, n_p = 1000, 6
+    s = np.concatenate([np.full(9000, 7), rng.integers(0, n_v, 7000), rng.integers(0, n_v, 20000)])
+    o = np.concatenate([rng.integers(0, n_v, 9000), np.full(7000, 7), rng.integers(0, n_v, 20000)])
+    p = np.concatenate([np.full(9000, 3), rng.integers(1, n_p + 1, 7000), rng.integers(1, n_p + 1, 20000)])
+    p[5000] = 6
+    g, ix = _graph(s, p, o, n_v, n_p)
+    for preds, dirs in _scan_cases(n_p, rng, 30):
+        want = np.ones(n_v, bool)
+        for q, d in zip(preds, dirs):
+            want &= ix.presence(int(d), int(q)).astype(bool)
+        got = _bits_to_bool(g.scan(preds, dirs), n_v)
+        assert np.array_equal(got, want), (preds, dirs)
+    assert _bits_to_bool(g.scan([3, 6], [0, 0]), n_v)[7]
+
+
+def _same(g, ix, pats, flags=0):
+    got = g.query(pats, sort=True, flags=flags)
+    want = ix.eval(pats, threads=4)
+    assert got.shape == want.shape, (pats, got.shape, want.shape)
+    assert np.array_equal(got, want), pats
+    return want
+
+
+@pytest.mark.parametrize("block", range(4))
+def test_eval_random_tiny_cases(block):
+    # the oracle is pinned to exhaustive enumeration on exactly these cases
+    for seed in range(block * 60, block * 60 + 60):
+        nv = 3 + seed % 5
+        npred = 1 + seed % 3
+        s, p, o = rdfgen.random_graph(seed, nv, npred, 4 + seed % 23)
+        g, ix = _graph(s, p, o, nv, npred)
+        q = rdfgen.random_bgp(seed + 7, nv, npred)
+        _same(g, ix, q)
+        _same(g, ix, q, flags=gs.PLAN_DIRECTION)
+
+
+def test_eval_rmat14_workload(rmat14):
+    w, (s, p, o), g, ix = rmat14
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    for q in rdfgen.queries(w, sm):
+        rows = _same(g, ix, q.patterns)
+        assert len(rows) >= 1     # the embedding that produced the query matches
+
+
+def test_eval_mid_size_random_shapes():
+    w = rdfgen.Workload("t", 12, 40000, 8, 1.0, 4242, 0, 0, 0)
+    s, p, o = rdfgen.graph(w)
+    g, ix = _graph(s, p, o, w.n_vertices, w.n_preds)
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    shapes = [rdfgen.star(2), rdfgen.star(4), rdfgen.chain(2), rdfgen.chain(4), rdfgen.cycle(3),
+              rdfgen.cycle(4), rdfgen.cycle(5), rdfgen.snowflake([1, 2]), rdfgen.snowflake([2, 2])]
+    n = 0
+    for i, sh in enumerate(shapes * 3):
+        q = sm.sample(sh, 77, i, 3e5)
+        _same(g, ix, q.patterns)
+        _same(g, ix, q.patterns, flags=gs.PLAN_DIRECTION)
+        n += 1
+    assert n == 27
+
+
+def test_eval_edge_cases(rmat14):
+    w, (s, p, o), g, ix = rmat14
+    t0 = (int(s[0]), int(p[0]), int(o[0]))
+    # exactly one row: an (s, p) pair with a single object
+    ts, tp, to = ix.triples()
+    key = ts.astype(np.int64) * 1000 + tp
+    u, first, cnt = np.unique(key, return_index=True, return_counts=True)
+    one = first[np.nonzero(cnt == 1)[0][0]]
+    assert len(_same(g, ix, [(int(ts[one]), int(tp[one]), -1)])) == 1
+    # constant-only pattern that holds / fails, next to a variable pattern
+    _same(g, ix, [(t0[0], t0[1], t0[2]), (-1, 1, -2)])
+    miss = (t0[0], t0[1], (t0[2] + 1) % w.n_vertices)
+    _same(g, ix, [miss, (-1, 1, -2)])
+    # empty: a predicate no vertex has twice in a row through a loop
+    _same(g, ix, [(-1, w.n_preds, -1), (-1, w.n_preds, -2), (-2, w.n_preds, -1)])
+    # self-loops and repeated patterns
+    _same(g, ix, [(-1, 1, -1)])
+    _same(g, ix, [(-1, 1, -2), (-1, 1, -2), (-2, 2, -2)])
+    # disconnected: a cross product of two components
+    _same(g, ix, [(-1, 5, t0[2]), (-2, 6, t0[2] ^ 1)])
+    _same(g, ix, [(-1, 9, -2), (-3, 16, -3)])
+    # two edges between the same pair of variables, both directions
+    _same(g, ix, [(-1, 1, -2), (-2, 2, -1), (-1, 3, -2)])
+    # every variable order of one chain gives the same rows
+    pats = np.array([(-1, 1, -2), (-2, 2, -3), (-3, 3, -4)], np.int64)
+    base = _same(g, ix, pats)
+    for perm in ([2, 1, 0], [1, 2, 0]):
+        assert np.array_equal(g.query(pats[perm]), base)
+
+
+def test_fetch_unsorted_is_a_permutation_and_overflow(rmat14):
+    w, _, g, ix = rmat14
+    pats = [(-1, 2, -2), (-2, 3, -3)]
+    r = g.eval(pats)
+    n, k = r.info()
+    assert n > 10
+    rows = r.fetch(sort=False)
+    srt = rows[np.lexsort(rows.T[::-1])]
+    assert np.array_equal(srt, ix.eval(pats))
+    small = np.empty((n - 1, k), np.int32)
+    with pytest.raises(gs.GsError) as e:
+        r.fetch(out=small)
+    assert e.value.status == 4
+    import torch
+    dev = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    r.fetch(sort=True, out=dev)
+    assert np.array_equal(dev.cpu().numpy(), srt)
+    assert r.time_ms() > 0
+    r.close()
+
+
+def test_workspace_retry(rmat14, monkeypatch):
+    # a tiny first workspace forces the overflow -> grow -> re-run path
+    w, _, g, ix = rmat14
+    monkeypatch.setenv("GS_ARENA_BYTES", "65536")
+    for pats in ([(-1, 1, -2), (-2, 1, -3)], [(-1, 2, -2), (-1, 3, -3), (-1, 4, -4)],
+                 [(-2, 8, -1), (-3, 1, -2), (-3, 5, -1)]):
+        _same(g, ix, pats)
+
+
+def test_hub_graph_expansion():
+    # one hub with 60000 out-edges: load-balanced expansion over a huge range
+    rng = np.random.default_rng(9)
+    n_v = 70000
+    s = np.concatenate([np.zeros(60000, np.int64), rng.integers(0, n_v, 60000)])
+    o = np.concatenate([np.arange(1, 60001), rng.integers(0, n_v, 60000)])
+    p = np.concatenate([np.ones(60000, np.int64), rng.integers(1, 4, 60000)])
+    g, ix = _graph(s, p, o, n_v, 3)
+    _same(g, ix, [(0, 1, -1), (-1, 2, -2)])
+    _same(g, ix, [(-1, 1, -2), (-2, 2, -3)])
+    _same(g, ix, [(-1, 1, -2), (-1, 1, -3), (-2, 3, -3)])
