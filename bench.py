@@ -40,6 +40,8 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the CPU oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", default="plain", choices=["plain", "scan"],
+                    help="plain: the query step; scan: the triple scan alone")
     return ap.parse_args()
 
 
@@ -106,6 +108,19 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def aggregate_rate(local_ms: float, units_per_rank: int, world: int, dist=None, device="cuda"):
+    """Whole-job rate of a replicated step: the units every rank processed
+    divided by the slowest rank's time (max over ranks). Returns (rate per
+    second, max milliseconds)."""
+    t_ms = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    return world * units_per_rank / (t_ms / 1000.0), t_ms
 
 
 def _dist():
@@ -206,7 +221,7 @@ def run_gsmart(args):
     plans = None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
 
-    def step(fetch: bool, lat=None, out_bufs=None):
+    def step(fetch: bool, lat=None, out_bufs=None, diag=None):
         launches, d2h, h2d = 0, 0, 0
         for i, q in enumerate(qs):
             t0 = time.perf_counter()
@@ -218,9 +233,13 @@ def run_gsmart(args):
                 r.fetch(sort=False, out=buf[: n * k].view(n, k).numpy())
                 d2h += 4 * n * k
                 h2d += q.patterns.nbytes
+            t1 = time.perf_counter()
             if lat is not None:
-                lat.append(time.perf_counter() - t0)
-            launches += r.stats()[1]
+                lat.append(t1 - t0)
+            dev_ms, nl = r.stats()
+            launches += nl
+            if diag is not None:
+                diag.append((q.shape, n, nl, dev_ms, 1000 * (t1 - t0)))
             r.close()
             plan.close()
         return launches, h2d, d2h
@@ -236,6 +255,12 @@ def run_gsmart(args):
 
     for _ in range(args.warmup):
         step(False)
+    diag = []
+    step(False, diag=diag)
+    if rank == 0:
+        for d in diag:
+            print("query %-12s rows %10d launches %3d device %.3f ms host %.3f ms" % d,
+                  file=sys.stderr)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lat = []
     step_ms = []
@@ -252,12 +277,36 @@ def run_gsmart(args):
             barrier()
             step_ms.append(ev0.elapsed_time(ev1))
     clocks = clk.summary()
-    t_ms = float(np.sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = ws * len(qs) * args.steps / (t_ms / 1000.0)
+    value, t_ms = aggregate_rate(float(np.sum(step_ms)), len(qs) * args.steps, ws, dist)
+
+    # batched: the same queries in one persistent launch per step
+    def batch_step():
+        plans = [g.plan(q.patterns) for q in qs]
+        b = g.eval_batch(plans, stream)
+        rows = b.rows()
+        st = b.stats()
+        b.close()
+        for pl in plans:
+            pl.close()
+        return rows, st
+
+    for _ in range(args.warmup):
+        batch_step()
+    b_ms, b_stats = [], None
+    for _ in range(args.steps):
+        flush.fill_(1)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        brows, b_stats = batch_step()
+        torch.cuda.synchronize()
+        b_ms.append(1000 * (time.perf_counter() - t0))
+    b_value, b_total = aggregate_rate(float(np.sum(b_ms)), len(qs) * args.steps, ws, dist)
+    batched = {"value": b_value, "unit": "queries/s",
+               "ms_per_step": b_total / args.steps, "device_ms_last": b_stats[0],
+               "kernel_launches_per_step": b_stats[1], "grid_path_queries": b_stats[2],
+               "rows_per_step": int(np.sum(brows)),
+               "timing": "host wall clock per step (plan + one batch launch + counts)"}
 
     # end to end: same step with answers copied into pinned host memory
     e2e_ms = []
@@ -269,12 +318,7 @@ def run_gsmart(args):
         _, h2d, d2h = step(True, None, out_bufs)
         torch.cuda.synchronize()
         e2e_ms.append(1000 * (time.perf_counter() - t0))
-    e2e_total = float(np.sum(e2e_ms))
-    if dist is not None:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = ws * len(qs) * args.steps / (e2e_total / 1000.0)
+    e2e_value, _ = aggregate_rate(float(np.sum(e2e_ms)), len(qs) * args.steps, ws, dist)
 
     # triple scan (Eq. 17 / Eq. 21 over the whole matrix): the bandwidth kernel
     peaks, which = _peaks()
@@ -322,6 +366,7 @@ def run_gsmart(args):
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
             "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
+            "batched": batched,
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": launches * args.steps,
         }), flush=True)
@@ -329,8 +374,60 @@ def run_gsmart(args):
         dist.destroy_process_group()
 
 
+def run_scan_only(args):
+    """The triple scan (Eq. 17 / Eq. 21 over the whole matrix) timed alone
+    on the workload graph: the query's grouped predicate set is the root
+    group of a constant-free star (three out-predicates, two in-predicates,
+    the most frequent ones)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2106_14038_b300 as gs
+    w = rdfgen.WORKLOADS[args.workload]
+    s, p, o = rdfgen.graph(w)
+    g = gs.Graph(s, p, o, w.n_vertices, w.n_preds)
+    del s, p, o
+    preds, dirs = [1, 2, 3, 1, 2], [0, 0, 0, 1, 1]
+    words = (w.n_vertices + 31) // 32
+    out = torch.empty(words, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        g.scan(preds, dirs, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            g.scan(preds, dirs, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    peaks, which = _peaks()
+    N, M = w.n_vertices, g.n_triples
+    alg = 2 * (4 * (N + 1) + 4 * M) + N // 8
+    t = float(np.mean(ms))
+    gbs = alg / (t / 1000.0) / 1e9
+    print(json.dumps({
+        "metric": "triple-scan HBM GB/s", "value": gbs, "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w.name, "scale": w.scale, "triples": M, "predicates": w.n_preds,
+                   "group": {"preds": preds, "dirs": dirs},
+                   "l2": "flushed before every step (256 MiB write)"},
+        "roofline": {"kernel": "triple scan", "bound": "hbm", "achieved": gbs,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                     "peak_source": which, "traffic": None, "algorithmic_bytes": alg},
+        "clocks": clk.summary(), "gpu_launches": 4 * args.steps,
+    }), flush=True)
+
+
 def main():
     args = _args()
+    if args.mode == "scan" and args.impl == "gsmart":
+        run_scan_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -111,7 +111,7 @@ gs_status gs_graph_export(const gs_graph* g, int by_column, uint32_t* ptr, uint3
  * GS_EINVAL when there is no variable, the variables are not dense, an id
  * is out of range, or n_patterns > GS_MAX_PATTERNS; GS_ENOTIMPL when a
  * variable has more than 8 distinct patterns to bound ends or 8 self-loops, or a
- * scan would test more than 31 distinct predicates in one direction.
+ * scan would test more than 16 distinct predicates in one direction.
  * Host only. */
 #define GS_PLAN_DEGREE 0u
 #define GS_PLAN_DIRECTION 1u
@@ -161,11 +161,89 @@ gs_status gs_fetch_bindings(gs_result* r, int32_t* dst, uint64_t cap_rows, int d
 gs_status gs_result_stats(gs_result* r, float* device_ms, uint32_t* kernel_launches);
 
 /* ------------------------------------------------------------------ */
+/* Batched evaluation: the same evaluation (Sec. 5, Sec. 7) of many plans in
+ * one persistent launch. Every CTA takes the next query from a device work
+ * counter and evaluates it on its own; answers of all queries share one
+ * device pool. Plans that need the full triple scan, and queries that
+ * outgrow one CTA's budget, are evaluated with the grid path of
+ * gs_eval_query afterwards, on the same stream. Answers are identical to
+ * gs_eval_query's.
+ *
+ *   plans        n plan pointers (host array; plans must outlive the batch)
+ * Enqueued on cuda_stream; gs_batch_info synchronizes. The pool starts at
+ * min(4 GiB, 1/4 of free memory) or the byte count in the environment
+ * variable GS_BATCH_POOL_BYTES; a query that does not fit it is handed to
+ * the grid path. */
+typedef struct gs_batch gs_batch;
+gs_status gs_eval_batch(gs_graph* g, const gs_plan* const* plans, uint32_t n, void* cuda_stream,
+                        gs_batch** out);
+
+/* Non-blocking: *done = 1 once everything gs_eval_batch enqueued has
+ * finished on the device (gs_batch_info then returns without waiting for the
+ * batch kernel; queries handed to the grid path still run there). */
+gs_status gs_batch_poll(gs_batch* b, int* done);
+
+/* Answer row counts: rows[q] for each query (rows may be NULL) and their sum.
+ * Synchronizes the batch's stream. */
+gs_status gs_batch_info(gs_batch* b, uint64_t* rows, uint64_t* total_rows);
+
+/* Answers of query q, as gs_fetch_bindings (row-major int32, n_vars columns;
+ * GS_EOVERFLOW when cap_rows is short). */
+gs_status gs_batch_fetch(gs_batch* b, uint32_t q, int32_t* dst, uint64_t cap_rows,
+                         int dst_on_device, int sort_rows);
+
+/* Device time from the batch's first enqueued operation to its last result,
+ * kernels launched, and queries handed to the grid path. Any out pointer may
+ * be NULL. Synchronizes. */
+gs_status gs_batch_stats(gs_batch* b, float* device_ms, uint32_t* kernel_launches,
+                         uint32_t* n_escalated);
+
+void gs_free_batch(gs_batch* b);
+
+/* ------------------------------------------------------------------ */
+/* Serving loop (continuous batching). The server keeps the graph resident
+ * and owns a worker thread and a pool of CUDA streams. Submitted plans wait
+ * in arrival order; the worker admits the waiting plans into a batch (as in
+ * gs_eval_batch) while the batch's device-memory estimate (per-CTA
+ * workspaces plus pool_bytes_per_query per query) fits the memory budget
+ * together with the batches in flight, and a stream is free. Batches
+ * admitted while others run overlap on the device. Answers are identical to
+ * gs_eval_query's; they stay on the device until the ticket is released.
+ * Submit / poll / fetch / release may be called from any host thread. */
+typedef struct gs_server gs_server;
+typedef struct {
+    uint32_t max_batch;              /* queries per batch (0: 1024) */
+    uint32_t n_streams;              /* batches in flight (0: 4) */
+    uint64_t memory_budget;          /* bytes of device memory (0: 40 GiB) */
+    uint32_t max_wait_us;            /* worker idle wait (0: 50) */
+    uint64_t pool_bytes_per_query;   /* answer pool share (0: 16 MiB) */
+} gs_server_config;
+
+gs_status gs_server_start(gs_graph* g, const gs_server_config* cfg, gs_server** out);
+/* Queue one plan (the plan must outlive its ticket). */
+gs_status gs_server_submit(gs_server* s, const gs_plan* plan, uint64_t* ticket);
+/* Non-blocking: *done = 1 when the answer is ready; then *rows and
+ * *latency_us (submission to completion, host clock) are set (may be NULL). */
+gs_status gs_server_poll(gs_server* s, uint64_t ticket, int* done, uint64_t* rows,
+                         double* latency_us);
+/* Answers of a finished ticket, as gs_fetch_bindings. */
+gs_status gs_server_fetch(gs_server* s, uint64_t ticket, int32_t* dst, uint64_t cap_rows,
+                          int dst_on_device, int sort_rows);
+/* Drop a finished ticket and its device memory share. */
+gs_status gs_server_release(gs_server* s, uint64_t ticket);
+/* Queries completed, batches launched, peak admitted device bytes. */
+gs_status gs_server_stats(gs_server* s, uint64_t* completed, uint64_t* batches,
+                          uint64_t* peak_bytes);
+/* Finish the queued work, free everything. */
+void gs_server_stop(gs_server* s);
+
+/* ------------------------------------------------------------------ */
 /* One grouped predicate selection on its own (Eq. 17, Eq. 21):
  *     v = AND_i  (dir_i == 0 ? A (x) u_{p_i} : A^T (x) u_{p_i})
  * i.e. bit x of v is 1 when row x of A holds every predicate p_i with
  * dir_i == 0 and column x holds every p_i with dir_i == 1 (Eq. 4, Eq. 5).
- *   preds, dirs   n host arrays, 1 <= n <= 31 per direction
+ *   preds, dirs   n host arrays (n >= 1), at most 16 distinct predicates per
+ *                 direction
  *   out_bits      device buffer of ceil(N/32) uint32 words; bit x of the
  *                 vector is bit (x % 32) of word x / 32; bits >= N are 0
  * Enqueued on cuda_stream (no synchronization). */

@@ -15,7 +15,7 @@ import numpy as np
 
 from ._build import LIB, build
 
-__all__ = ["Graph", "Plan", "Result", "GsError", "load_library", "PLAN_DEGREE",
+__all__ = ["Graph", "Plan", "Result", "Batch", "Server", "GsError", "TorchAllocator", "load_library", "PLAN_DEGREE",
            "PLAN_DIRECTION", "build"]
 
 PLAN_DEGREE = 0
@@ -26,7 +26,10 @@ _STATUS = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOMEM", 3: "GS_ECUDA", 4: "GS_EOV
 EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_query",
             "gs_plan_describe", "gs_eval_query", "gs_result_info", "gs_fetch_bindings",
             "gs_result_stats", "gs_scan_candidates", "gs_free_graph", "gs_free_plan",
-            "gs_free_result", "gs_last_error"]
+            "gs_free_result", "gs_last_error", "gs_eval_batch", "gs_batch_info",
+            "gs_batch_fetch", "gs_batch_stats", "gs_free_batch", "gs_batch_poll",
+            "gs_server_start", "gs_server_submit", "gs_server_poll", "gs_server_fetch",
+            "gs_server_release", "gs_server_stats", "gs_server_stop"]
 
 
 class GsError(RuntimeError):
@@ -35,8 +38,46 @@ class GsError(RuntimeError):
         self.status = status
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class _Allocator(ctypes.Structure):
-    _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p)]
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator
+    (passed through the C ABI's gs_allocator hook). `fail_after` makes the
+    n-th and later allocations fail (returns NULL), for failure tests."""
+
+    def __init__(self, device: int = 0, fail_after: int | None = None):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.fail_after = fail_after
+        self.calls = 0
+        self.live = {}
+
+        def _alloc(nbytes, stream, ctx):
+            self.calls += 1
+            if self.fail_after is not None and self.calls >= self.fail_after:
+                return None
+            try:
+                ptr = self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, stream)
+            except Exception:
+                return None
+            self.live[ptr] = nbytes
+            return ptr
+
+        def _free(ptr, stream, ctx):
+            if ptr:
+                self.live.pop(ptr, None)
+                self._torch.cuda.caching_allocator_delete(ptr)
+
+        self._cb_alloc = _ALLOC_FN(_alloc)
+        self._cb_free = _FREE_FN(_free)
+        self.struct = _Allocator(self._cb_alloc, self._cb_free, None)
 
 
 _lib = None
@@ -65,12 +106,24 @@ def load_library(path: str | None = None):
         "gs_fetch_bindings": [vp, vp, u64, i32, i32],
         "gs_result_stats": [vp, P(ctypes.c_float), P(u32)],
         "gs_scan_candidates": [vp, vp, vp, u32, vp, vp],
+        "gs_eval_batch": [vp, vp, u32, vp, P(vp)],
+        "gs_batch_info": [vp, vp, P(u64)],
+        "gs_batch_fetch": [vp, u32, vp, u64, i32, i32],
+        "gs_batch_stats": [vp, P(ctypes.c_float), P(u32), P(u32)],
+        "gs_batch_poll": [vp, P(i32)],
+        "gs_server_start": [vp, vp, P(vp)],
+        "gs_server_submit": [vp, vp, P(u64)],
+        "gs_server_poll": [vp, u64, P(i32), P(u64), P(ctypes.c_double)],
+        "gs_server_fetch": [vp, u64, vp, u64, i32, i32],
+        "gs_server_release": [vp, u64],
+        "gs_server_stats": [vp, P(u64), P(u64), P(u64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = i32
-    for name in ("gs_free_graph", "gs_free_plan", "gs_free_result"):
+    for name in ("gs_free_graph", "gs_free_plan", "gs_free_result", "gs_free_batch",
+                 "gs_server_stop"):
         f = getattr(lib, name)
         f.argtypes = [vp]
         f.restype = None
@@ -101,9 +154,11 @@ def _host_u32(a):
 class Graph:
     """The RDF matrix resident on the device (CSR + CSC with labels)."""
 
-    def __init__(self, s, p, o, n_vertices: int, n_predicates: int, stream=None):
+    def __init__(self, s, p, o, n_vertices: int, n_predicates: int, stream=None,
+                 allocator: "TorchAllocator | None" = None):
         lib = load_library()
         self._keep = None
+        self._allocator = allocator      # callbacks must outlive the graph
         on_dev = hasattr(s, "is_cuda") and s.is_cuda
         if on_dev:
             import torch
@@ -117,7 +172,8 @@ class Graph:
             n = len(s)
             self._keep = (s, p, o)
         h = ctypes.c_void_p()
-        _check(lib.gs_load_triples(*ptrs, n, n_vertices, n_predicates, int(on_dev), None,
+        aptr = ctypes.byref(allocator.struct) if allocator is not None else None
+        _check(lib.gs_load_triples(*ptrs, n, n_vertices, n_predicates, int(on_dev), aptr,
                                    _stream_handle(stream), ctypes.byref(h)))
         self._keep = None
         self._h = h
@@ -163,6 +219,15 @@ class Graph:
             return r.fetch(sort=sort)
         finally:
             r.close()
+
+    def eval_batch(self, plans, stream=None) -> "Batch":
+        """Evaluate many plans (or pattern arrays) in one persistent launch."""
+        plans = [p if isinstance(p, Plan) else self.plan(p) for p in plans]
+        arr = (ctypes.c_void_p * max(1, len(plans)))(*[p._h.value for p in plans])
+        h = ctypes.c_void_p()
+        _check(_lib.gs_eval_batch(self._h, arr, len(plans), _stream_handle(stream),
+                                  ctypes.byref(h)))
+        return Batch(h, plans)
 
     def scan(self, preds, dirs, out=None, stream=None):
         """Eq. 17 / Eq. 21 on its own: a torch int32 tensor of ceil(N/32)
@@ -223,6 +288,111 @@ class Plan:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    def __init__(self, h, plans):
+        self._h = h
+        self._plans = plans       # the plans must outlive the batch
+
+    def rows(self):
+        """Answer row count of every query (numpy uint64)."""
+        n = len(self._plans)
+        out = np.zeros(max(1, n), np.uint64)
+        tot = ctypes.c_uint64()
+        _check(_lib.gs_batch_info(self._h, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(tot)))
+        return out[:n]
+
+    def fetch(self, q: int, sort: bool = True):
+        n = int(self.rows()[q])
+        k = self._plans[q].n_vars
+        out = np.empty((n, k), np.int32)
+        _check(_lib.gs_batch_fetch(self._h, q, out.ctypes.data_as(ctypes.c_void_p), n, 0, int(sort)))
+        return out
+
+    def stats(self):
+        """(device milliseconds, kernels launched, queries sent to the grid path)."""
+        ms = ctypes.c_float()
+        nl = ctypes.c_uint32()
+        ne = ctypes.c_uint32()
+        _check(_lib.gs_batch_stats(self._h, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(ne)))
+        return float(ms.value), int(nl.value), int(ne.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.gs_free_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("n_streams", ctypes.c_uint32),
+                ("memory_budget", ctypes.c_uint64), ("max_wait_us", ctypes.c_uint32),
+                ("pool_bytes_per_query", ctypes.c_uint64)]
+
+
+class Server:
+    """Continuous-batching server over a resident graph (gs_server_*)."""
+
+    def __init__(self, graph: Graph, max_batch: int = 0, n_streams: int = 0,
+                 memory_budget: int = 0, max_wait_us: int = 0, pool_bytes_per_query: int = 0):
+        cfg = _ServerConfig(max_batch, n_streams, memory_budget, max_wait_us, pool_bytes_per_query)
+        h = ctypes.c_void_p()
+        _check(_lib.gs_server_start(graph._h, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._graph = graph
+        self._plans = {}
+
+    def submit(self, plan: "Plan") -> int:
+        t = ctypes.c_uint64()
+        _check(_lib.gs_server_submit(self._h, plan._h, ctypes.byref(t)))
+        self._plans[t.value] = plan
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """(done, rows, latency_us)."""
+        d = ctypes.c_int()
+        n = ctypes.c_uint64()
+        lat = ctypes.c_double()
+        _check(_lib.gs_server_poll(self._h, ticket, ctypes.byref(d), ctypes.byref(n),
+                                   ctypes.byref(lat)))
+        return bool(d.value), int(n.value), float(lat.value)
+
+    def fetch(self, ticket: int, sort: bool = True):
+        done, n, _ = self.poll(ticket)
+        if not done:
+            raise RuntimeError("ticket %d is not finished" % ticket)
+        k = self._plans[ticket].n_vars
+        out = np.empty((n, k), np.int32)
+        _check(_lib.gs_server_fetch(self._h, ticket, out.ctypes.data_as(ctypes.c_void_p), n, 0,
+                                    int(sort)))
+        return out
+
+    def release(self, ticket: int):
+        _check(_lib.gs_server_release(self._h, ticket))
+        self._plans.pop(ticket, None)
+
+    def stats(self):
+        """(completed queries, batches launched, peak admitted device bytes)."""
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib.gs_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return int(a.value), int(b.value), int(c.value)
+
+    def stop(self):
+        if getattr(self, "_h", None):
+            _lib.gs_server_stop(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.stop()
         except Exception:
             pass
 

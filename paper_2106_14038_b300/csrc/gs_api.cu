@@ -14,6 +14,51 @@ const char* last_error();
 
 using namespace gs;
 
+namespace gs {
+
+// ---- device row sort (lexicographic, LSD over columns) ----
+
+__global__ void k_sort_keys(const int32_t* __restrict__ rows, uint32_t k, uint32_t c, uint64_t n,
+                            uint64_t* __restrict__ keys, int first) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t perm = first ? i : (keys[i] & 0xffffffffull);
+        uint32_t v = (uint32_t)rows[perm * k + c];
+        keys[i] = ((uint64_t)v << 32) | perm;
+    }
+}
+
+__global__ void k_sort_gather(const int32_t* __restrict__ rows, uint32_t k, uint64_t n,
+                              const uint64_t* __restrict__ keys, int32_t* __restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t perm = keys[i] & 0xffffffffull;
+        for (uint32_t j = 0; j < k; ++j) out[i * k + j] = rows[perm * k + j];
+    }
+}
+
+gs_status sort_rows_on_device(const gs_graph* g, const int32_t* rows, uint64_t n, uint32_t k,
+                        int32_t* out, cudaStream_t st) {
+    if (n >= (1ull << 32)) { set_error("gs_fetch_bindings: sorting needs fewer than 2^32 rows"); return GS_ENOTIMPL; }
+    uint64_t* k0 = (uint64_t*)g->alloc.get(8 * n, st);
+    uint64_t* k1 = (uint64_t*)g->alloc.get(8 * n, st);
+    if (!k0 || !k1) { g->alloc.put(k0, st); g->alloc.put(k1, st); set_error("gs_fetch_bindings: out of device memory for sorting"); return GS_ENOMEM; }
+    const int nb = g->n_blocks;
+    gs_status rc = GS_OK;
+    for (int c = (int)k - 1; c >= 0 && rc == GS_OK; --c) {
+        k_sort_keys<<<nb, kThreads, 0, st>>>(rows, k, (uint32_t)c, n, k0, c == (int)k - 1);
+        rc = radix_sort_u64(g, &k0, &k1, n, 32, 64, st);
+    }
+    if (rc == GS_OK) k_sort_gather<<<nb, kThreads, 0, st>>>(rows, k, n, k0, out);
+    cudaError_t e = cudaGetLastError();
+    g->alloc.put(k0, st);
+    g->alloc.put(k1, st);
+    if (rc == GS_OK && e != cudaSuccess) rc = cuda_fail(e, "row sort");
+    return rc;
+}
+
+}  // namespace gs
+
 struct gs_result {
     gs_graph* g = nullptr;
     gs_plan plan;
@@ -26,6 +71,7 @@ struct gs_result {
     uint64_t list_stride = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ready = false;
+    int mode = 0;             // 0: grid path, 1: single-block kernel
     uint32_t launches = 0;
     uint64_t rows = 0;
     uint64_t out_off = 0;
@@ -35,6 +81,7 @@ namespace {
 
 constexpr uint64_t kArenaMin = 64ull << 20;
 constexpr uint64_t kArenaDefault = 512ull << 20;
+constexpr uint64_t kArenaSmall = 64ull << 20;   // enough for the single-block budgets
 constexpr int kMaxRetries = 16;
 
 ExecDev exec_view(gs_result* r) {
@@ -53,7 +100,9 @@ ExecDev exec_view(gs_result* r) {
 
 gs_status enqueue(gs_result* r) {
     GS_CUDA(cudaEventRecord(r->ev0, r->st));
-    gs_status rc = enqueue_eval(r->g, &r->plan, exec_view(r), r->work, &r->launches, r->st);
+    gs_status rc = r->mode == 1
+        ? enqueue_small(&r->plan, exec_view(r), &r->launches, r->st)
+        : enqueue_eval(r->g, &r->plan, exec_view(r), r->work, &r->launches, r->st);
     if (rc != GS_OK) return rc;
     GS_CUDA(cudaEventRecord(r->ev1, r->st));
     r->ready = false;
@@ -69,6 +118,19 @@ gs_status wait_result(gs_result* r) {
         if (head.status & kStHuge) {
             set_error("gs_eval_query: the answer has more than 2^40 rows under one binding");
             return GS_ENOMEM;
+        }
+        if (head.status & kStEscalate) {
+            // the single-block kernel handed the query back: run the grid path
+            r->mode = 0;
+            if (r->arena_bytes < kArenaDefault) {
+                r->g->alloc.put(r->arena, r->st);
+                r->arena = (uint8_t*)r->g->alloc.get(kArenaDefault, r->st);
+                if (!r->arena) { set_error("gs_eval_query: cannot allocate the workspace"); return GS_ENOMEM; }
+                r->arena_bytes = kArenaDefault;
+            }
+            gs_status rc = enqueue(r);
+            if (rc != GS_OK) return rc;
+            continue;
         }
         if (!(head.status & kStOverflow)) {
             const int last = r->plan.n_levels - 1;
@@ -115,47 +177,6 @@ void release(gs_result* r) {
     if (r->ev0) cudaEventDestroy(r->ev0);
     if (r->ev1) cudaEventDestroy(r->ev1);
     delete r;
-}
-
-// ---- device row sort (lexicographic, LSD over columns) ----
-
-__global__ void k_sort_keys(const int32_t* __restrict__ rows, uint32_t k, uint32_t c, uint64_t n,
-                            uint64_t* __restrict__ keys, int first) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t perm = first ? i : (keys[i] & 0xffffffffull);
-        uint32_t v = (uint32_t)rows[perm * k + c];
-        keys[i] = ((uint64_t)v << 32) | perm;
-    }
-}
-
-__global__ void k_sort_gather(const int32_t* __restrict__ rows, uint32_t k, uint64_t n,
-                              const uint64_t* __restrict__ keys, int32_t* __restrict__ out) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t perm = keys[i] & 0xffffffffull;
-        for (uint32_t j = 0; j < k; ++j) out[i * k + j] = rows[perm * k + j];
-    }
-}
-
-gs_status sort_rows_dev(const gs_graph* g, const int32_t* rows, uint64_t n, uint32_t k,
-                        int32_t* out, cudaStream_t st) {
-    if (n >= (1ull << 32)) { set_error("gs_fetch_bindings: sorting needs fewer than 2^32 rows"); return GS_ENOTIMPL; }
-    uint64_t* k0 = (uint64_t*)g->alloc.get(8 * n, st);
-    uint64_t* k1 = (uint64_t*)g->alloc.get(8 * n, st);
-    if (!k0 || !k1) { g->alloc.put(k0, st); g->alloc.put(k1, st); set_error("gs_fetch_bindings: out of device memory for sorting"); return GS_ENOMEM; }
-    const int nb = g->n_blocks;
-    gs_status rc = GS_OK;
-    for (int c = (int)k - 1; c >= 0 && rc == GS_OK; --c) {
-        k_sort_keys<<<nb, kThreads, 0, st>>>(rows, k, (uint32_t)c, n, k0, c == (int)k - 1);
-        rc = radix_sort_u64(g, &k0, &k1, n, 32, 64, st);
-    }
-    if (rc == GS_OK) k_sort_gather<<<nb, kThreads, 0, st>>>(rows, k, n, k0, out);
-    cudaError_t e = cudaGetLastError();
-    g->alloc.put(k0, st);
-    g->alloc.put(k1, st);
-    if (rc == GS_OK && e != cudaSuccess) rc = cuda_fail(e, "row sort");
-    return rc;
 }
 
 void set_pool_threshold(int dev) {
@@ -252,7 +273,10 @@ gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint
     return GS_OK;
 }
 
-gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out) {
+}  // extern "C"
+
+gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
+                              gs_result** out) {
     if (!g || !plan || !out) { set_error("gs_eval_query: NULL argument"); return GS_EINVAL; }
     *out = nullptr;
     if (plan->N == 0) {   // planned without a graph: check the ids now
@@ -289,10 +313,12 @@ gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_
         r->lists = (uint32_t*)g->alloc.get(4ull * g->N * plan->n_levels, r->st);
         if (!r->lists) { set_error("gs_eval_query: out of device memory"); rc = GS_ENOMEM; }
     }
+    r->mode = (small_eligible(plan) && !force_grid) ? 1 : 0;
     if (rc == GS_OK) {
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
         uint64_t want = std::max<uint64_t>(kArenaMin, std::min<uint64_t>(kArenaDefault, free_b / 8));
+        if (r->mode == 1) want = kArenaSmall;
         if (const char* env = getenv("GS_ARENA_BYTES")) {   // initial workspace size
             unsigned long long v = strtoull(env, nullptr, 10);
             if (v >= 4096) want = v;
@@ -305,6 +331,13 @@ gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_
     if (rc != GS_OK) { release(r); return rc; }
     *out = r;
     return GS_OK;
+}
+
+extern "C" {
+
+gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out) {
+    const char* how = getenv("GS_EXEC");   // "grid" forces the grid path
+    return eval_query_path(g, plan, cuda_stream, how && !strcmp(how, "grid"), out);
 }
 
 gs_status gs_result_info(gs_result* r, uint64_t* n_rows, uint32_t* n_vars) {
@@ -344,7 +377,7 @@ gs_status gs_fetch_bindings(gs_result* r, int32_t* dst, uint64_t cap_rows, int d
     if (sort_rows && r->rows > 1) {
         int32_t* tmp = (int32_t*)r->g->alloc.get(bytes, r->st);
         if (!tmp) { set_error("gs_fetch_bindings: out of device memory for sorting"); return GS_ENOMEM; }
-        rc = sort_rows_dev(r->g, src, r->rows, k, tmp, r->st);
+        rc = sort_rows_on_device(r->g, src, r->rows, k, tmp, r->st);
         if (rc == GS_OK) {
             cudaError_t e = cudaMemcpyAsync(dst, tmp, bytes, kind, r->st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(r->st);

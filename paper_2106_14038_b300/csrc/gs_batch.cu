@@ -1,0 +1,307 @@
+// Batched evaluation: many queries in one persistent launch (k_batch in
+// gs_small.cu). The host packs the schedules of all queries that fit the
+// single-block record into one staging buffer (one copy to the device),
+// launches one CTA per resident slot; every CTA pulls queries from a device
+// counter and evaluates them in its own workspace, writing answers into a
+// shared pool. Queries that need the full triple scan, do not fit a record,
+// or outgrow the per-CTA budgets run on the grid path afterwards, each as
+// an ordinary result.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gs_device.cuh"
+#include "gs_exec.h"
+#include "gs_qrec.h"
+
+using namespace gs;
+
+struct gs_batch {
+    gs_graph* g = nullptr;
+    cudaStream_t st = nullptr;
+    uint32_t n = 0;
+    std::vector<const gs_plan*> plans;
+    std::vector<int32_t> n_vars;
+    std::vector<uint8_t> in_kernel;        // 1: evaluated by k_batch
+    std::vector<uint32_t> kidx;            // kernel index -> query
+    uint8_t* dev = nullptr;                // records | offsets | results | counters
+    uint8_t* slots = nullptr;
+    uint8_t* pool = nullptr;
+    uint64_t pool_bytes = 0;
+    BatchResult* res_dev = nullptr;
+    std::vector<BatchResult> res;
+    std::vector<gs_result*> sub;           // grid-path results
+    uint8_t* staging = nullptr;            // pinned host
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    uint32_t launches = 0, escalated = 0;
+    int blocks = 0;
+    cudaEvent_t ev_enq = nullptr;          // after everything gs_eval_batch enqueued
+    bool ready = false;
+};
+
+namespace {
+
+constexpr uint64_t kBatchCand = 1ull << 16;
+constexpr uint64_t kBatchRows = 1ull << 20;
+constexpr uint64_t kSlotBytes = 24ull << 20;
+constexpr uint64_t kPoolDefault = 4ull << 30;
+
+int batch_blocks(const gs_graph* g) {
+    int per_sm = batch_blocks_per_sm();
+    if (const char* e = getenv("GS_BATCH_BLOCKS_PER_SM")) per_sm = std::max(1, std::min(per_sm, atoi(e)));
+    return g->sm_count * per_sm;
+}
+
+gs_status finish(gs_batch* b) {
+    if (b->ready) return GS_OK;
+    GS_CUDA(cudaStreamSynchronize(b->st));
+    const uint32_t nk = (uint32_t)b->kidx.size();
+    if (b->res_dev && nk) {
+        std::vector<BatchResult> kr(nk);
+        GS_CUDA(cudaMemcpy(kr.data(), b->res_dev, sizeof(BatchResult) * nk, cudaMemcpyDeviceToHost));
+        for (uint32_t i = 0; i < nk; ++i) b->res[b->kidx[i]] = kr[i];
+    }
+    // grid path for the queries the kernel handed back
+    for (uint32_t q = 0; q < b->n; ++q) {
+        if (!b->in_kernel[q] || b->res[q].status == 0) continue;
+        b->escalated++;
+        gs_result* r = nullptr;
+        gs_status rc = eval_query_path(b->g, b->plans[q], (void*)b->st, 1, &r);
+        if (rc != GS_OK) return rc;
+        b->sub[q] = r;
+    }
+    for (uint32_t q = 0; q < b->n; ++q) {
+        if (!b->sub[q]) continue;
+        uint64_t rows = 0;
+        gs_status rc = gs_result_info(b->sub[q], &rows, nullptr);
+        if (rc != GS_OK) return rc;
+        uint32_t nl = 0;
+        gs_result_stats(b->sub[q], nullptr, &nl);
+        b->launches += nl;
+        b->res[q].rows = rows;
+    }
+    GS_CUDA(cudaEventRecord(b->ev1, b->st));
+    GS_CUDA(cudaEventSynchronize(b->ev1));
+    b->ready = true;
+    return GS_OK;
+}
+
+void release(gs_batch* b) {
+    if (!b) return;
+    if (b->st || b->g) cudaStreamSynchronize(b->st);
+    for (gs_result* r : b->sub) gs_free_result(r);
+    if (b->g) {
+        b->g->alloc.put(b->dev, b->st);
+        b->g->alloc.put(b->slots, b->st);
+        b->g->alloc.put(b->pool, b->st);
+    }
+    if (b->staging) cudaFreeHost(b->staging);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->ev_enq) cudaEventDestroy(b->ev_enq);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_eval_batch(gs_graph* g, const gs_plan* const* plans, uint32_t n, void* cuda_stream,
+                        gs_batch** out) {
+    return eval_batch_ex(g, plans, n, cuda_stream, 0, 0, out);
+}
+
+}  // extern "C"
+
+gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n, void* cuda_stream,
+                            int max_blocks, uint64_t pool_bytes, gs_batch** out) {
+    if (!g || !out || (n && !plans)) { set_error("gs_eval_batch: NULL argument"); return GS_EINVAL; }
+    *out = nullptr;
+    for (uint32_t q = 0; q < n; ++q) {
+        if (!plans[q]) { set_error("gs_eval_batch: plan %u is NULL", q); return GS_EINVAL; }
+        if (plans[q]->N != 0 && (plans[q]->N != g->N || plans[q]->P != g->P)) {
+            set_error("gs_eval_batch: plan %u was made for another graph", q);
+            return GS_EINVAL;
+        }
+    }
+    gs_batch* b = new (std::nothrow) gs_batch();
+    if (!b) { set_error("gs_eval_batch: host out of memory"); return GS_ENOMEM; }
+    b->g = g;
+    b->st = (cudaStream_t)cuda_stream;
+    b->n = n;
+    b->plans.assign(plans, plans + n);
+    b->n_vars.resize(n);
+    b->in_kernel.assign(n, 0);
+    b->res.assign(n, BatchResult{0, 0, 0, 0});
+    b->sub.assign(n, nullptr);
+    if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_enq, cudaEventDisableTiming) != cudaSuccess) {
+        gs_status rc = cuda_fail(cudaGetLastError(), "cudaEventCreate");
+        release(b);
+        return rc;
+    }
+    // pack records
+    std::vector<uint64_t> off(n, 0);
+    uint64_t total = 0;
+    uint32_t n_in = 0;
+    for (uint32_t q = 0; q < n; ++q) {
+        b->n_vars[q] = plans[q]->n_vars;
+        if (rec_fits(plans[q])) {
+            b->in_kernel[q] = 1;
+            off[n_in] = total;
+            b->kidx.push_back(q);
+            total += sizeof(QHdr) + plans[q]->n_levels * sizeof(LevelSpec) +
+                     plans[q]->n_leaves * sizeof(LeafSpec) + 16;
+            total = (total + 15) & ~15ull;
+            ++n_in;
+        }
+    }
+    const uint64_t off_bytes = 8ull * n_in, res_bytes = sizeof(BatchResult) * (uint64_t)n_in;
+    const uint64_t dev_bytes = total + off_bytes + res_bytes + 256;
+    if (cudaMallocHost(&b->staging, total + off_bytes + 16) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("gs_eval_batch: cannot allocate pinned staging memory");
+        release(b);
+        return GS_ENOMEM;
+    }
+    for (uint32_t i = 0; i < n_in; ++i) pack_record(plans[b->kidx[i]], b->staging + off[i]);
+    std::memcpy(b->staging + total, off.data(), off_bytes);
+    b->dev = (uint8_t*)g->alloc.get(dev_bytes, b->st);
+    int blocks = batch_blocks(g);
+    if (max_blocks > 0) blocks = std::min(blocks, max_blocks);
+    blocks = std::max(1, std::min<int>(blocks, (int)std::max<uint32_t>(1, n_in)));
+    b->blocks = blocks;
+    b->slots = (uint8_t*)g->alloc.get(kSlotBytes * blocks, b->st);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    b->pool_bytes = std::min<uint64_t>(kPoolDefault, free_b / 4);
+    if (pool_bytes) b->pool_bytes = pool_bytes;
+    if (const char* e = getenv("GS_BATCH_POOL_BYTES")) b->pool_bytes = strtoull(e, nullptr, 10);
+    b->pool = (uint8_t*)g->alloc.get(std::max<uint64_t>(b->pool_bytes, 256), b->st);
+    if (!b->dev || !b->slots || !b->pool) {
+        set_error("gs_eval_batch: out of device memory");
+        release(b);
+        return GS_ENOMEM;
+    }
+    gs_status rc = GS_OK;
+    cudaError_t e = cudaEventRecord(b->ev0, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->dev, b->staging, total + off_bytes, cudaMemcpyHostToDevice, b->st);
+    b->res_dev = (BatchResult*)(b->dev + total + off_bytes);
+    uint32_t* counters = (uint32_t*)(b->dev + total + off_bytes + res_bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 64, b->st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "gs_eval_batch");
+    if (rc == GS_OK && n_in) {
+        BatchDev B{};
+        B.out = dview(g->out);
+        B.in = dview(g->in);
+        B.recs = b->dev;
+        B.rec_off = (const uint64_t*)(b->dev + total);
+        B.n = n_in;
+        B.slots = b->slots;
+        B.slot_bytes = kSlotBytes;
+        (void)0;
+        B.pool = b->pool;
+        B.pool_bytes = b->pool_bytes;
+        B.pool_top = (unsigned long long*)(counters + 2);
+        B.next = counters;
+        B.res = b->res_dev;
+        B.cand_budget = kBatchCand;
+        B.row_budget = kBatchRows;
+        rc = enqueue_batch(B, blocks, b->st);
+        b->launches = 1;
+    }
+    // plans outside the record format go straight to the grid path (same stream)
+    for (uint32_t q = 0; q < n && rc == GS_OK; ++q)
+        if (!b->in_kernel[q]) rc = eval_query_path(g, plans[q], (void*)b->st, 1, &b->sub[q]);
+    if (rc == GS_OK) {
+        cudaError_t e2 = cudaEventRecord(b->ev_enq, b->st);
+        if (e2 != cudaSuccess) rc = cuda_fail(e2, "gs_eval_batch");
+    }
+    if (rc != GS_OK) { release(b); return rc; }
+    *out = b;
+    return GS_OK;
+}
+
+uint64_t gs::batch_device_bytes(const gs_batch* b) {
+    return kSlotBytes * (uint64_t)b->blocks + b->pool_bytes;
+}
+
+extern "C" {
+
+gs_status gs_batch_poll(gs_batch* b, int* done) {
+    if (!b || !done) { set_error("gs_batch_poll: NULL argument"); return GS_EINVAL; }
+    if (b->ready) { *done = 1; return GS_OK; }
+    cudaError_t e = cudaEventQuery(b->ev_enq);
+    if (e == cudaErrorNotReady) { *done = 0; return GS_OK; }
+    if (e != cudaSuccess) return cuda_fail(e, "gs_batch_poll");
+    *done = 1;   // the launch finished; gs_batch_info completes any hand-backs
+    return GS_OK;
+}
+
+gs_status gs_batch_info(gs_batch* b, uint64_t* rows, uint64_t* total_rows) {
+    if (!b) { set_error("gs_batch_info: batch is NULL"); return GS_EINVAL; }
+    gs_status rc = finish(b);
+    if (rc != GS_OK) return rc;
+    uint64_t t = 0;
+    for (uint32_t q = 0; q < b->n; ++q) {
+        if (rows) rows[q] = b->res[q].rows;
+        t += b->res[q].rows;
+    }
+    if (total_rows) *total_rows = t;
+    return GS_OK;
+}
+
+gs_status gs_batch_fetch(gs_batch* b, uint32_t q, int32_t* dst, uint64_t cap_rows, int dst_on_device,
+                         int sort_rows) {
+    if (!b) { set_error("gs_batch_fetch: batch is NULL"); return GS_EINVAL; }
+    if (q >= b->n) { set_error("gs_batch_fetch: query %u of %u", q, b->n); return GS_EINVAL; }
+    gs_status rc = finish(b);
+    if (rc != GS_OK) return rc;
+    if (b->sub[q]) return gs_fetch_bindings(b->sub[q], dst, cap_rows, dst_on_device, sort_rows);
+    const uint64_t rows = b->res[q].rows;
+    if (cap_rows < rows) {
+        set_error("gs_batch_fetch: buffer holds %llu rows, the answer has %llu",
+                  (unsigned long long)cap_rows, (unsigned long long)rows);
+        return GS_EOVERFLOW;
+    }
+    if (rows == 0) return GS_OK;
+    if (!dst) { set_error("gs_batch_fetch: dst is NULL"); return GS_EINVAL; }
+    const uint32_t k = (uint32_t)b->n_vars[q];
+    const uint64_t bytes = 4ull * rows * k;
+    const int32_t* src = (const int32_t*)(b->pool + b->res[q].off);
+    cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (sort_rows && rows > 1) {
+        int32_t* tmp = (int32_t*)b->g->alloc.get(bytes, b->st);
+        if (!tmp) { set_error("gs_batch_fetch: out of device memory for sorting"); return GS_ENOMEM; }
+        rc = sort_rows_on_device(b->g, src, rows, k, tmp, b->st);
+        if (rc == GS_OK) {
+            cudaError_t e = cudaMemcpyAsync(dst, tmp, bytes, kind, b->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "gs_batch_fetch copy");
+        }
+        b->g->alloc.put(tmp, b->st);
+        cudaStreamSynchronize(b->st);
+        return rc;
+    }
+    GS_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, b->st));
+    GS_CUDA(cudaStreamSynchronize(b->st));
+    return GS_OK;
+}
+
+gs_status gs_batch_stats(gs_batch* b, float* device_ms, uint32_t* kernel_launches,
+                         uint32_t* n_escalated) {
+    if (!b) { set_error("gs_batch_stats: batch is NULL"); return GS_EINVAL; }
+    gs_status rc = finish(b);
+    if (rc != GS_OK) return rc;
+    if (device_ms) GS_CUDA(cudaEventElapsedTime(device_ms, b->ev0, b->ev1));
+    if (kernel_launches) *kernel_launches = b->launches;
+    if (n_escalated) *n_escalated = b->escalated;
+    return GS_OK;
+}
+
+void gs_free_batch(gs_batch* b) { release(b); }
+
+}  // extern "C"

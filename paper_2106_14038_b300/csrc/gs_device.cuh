@@ -13,41 +13,103 @@ namespace gs {
 
 __device__ __forceinline__ uint32_t ld(const uint32_t* p) { return __ldg(p); }
 
-// First position in [lo, hi) of the sorted array a whose value is >= key.
+// Searches in sorted uint32 ranges. They are latency-bound gathers, so they
+// trade a few extra loads for fewer dependent round trips: a range of at
+// most kShort entries is read with independent 16-byte loads and counted;
+// a longer one is cut by 8 parallel probes per round (9-ary search).
+constexpr uint32_t kShort = 32;
+
+// Number of entries of a[lo..hi) (hi - lo <= kShort) below key and equal to key.
+__device__ __forceinline__ void count_short(const uint32_t* __restrict__ a, uint32_t lo,
+                                            uint32_t hi, uint32_t key, uint32_t& below,
+                                            uint32_t& equal) {
+    const uint4* v = reinterpret_cast<const uint4*>(a);
+    const uint32_t q0 = lo >> 2, q1 = (hi + 3) >> 2;   // at most 9 words
+    uint4 x[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) x[i] = (q0 + i < q1) ? __ldg(v + q0 + i) : make_uint4(0, 0, 0, 0);
+    below = 0;
+    equal = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const uint32_t k = (q0 + i) << 2;
+        const uint32_t e[4] = {x[i].x, x[i].y, x[i].z, x[i].w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const bool in = k + t >= lo && k + t < hi;
+            below += in && e[t] < key;
+            equal += in && e[t] == key;
+        }
+    }
+}
+
+// First position in [lo, hi) of the sorted array a whose value is >= key
+// (hi when there is none).
 __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t lo,
                                                     uint32_t hi, uint32_t key) {
-    while (lo < hi) {
-        uint32_t mid = lo + ((hi - lo) >> 1);
-        if (ld(a + mid) < key) lo = mid + 1; else hi = mid;
+    while (hi - lo > kShort) {
+        const uint32_t n = hi - lo;
+        uint32_t c = 0, last_lt = lo, first_ge = hi;
+        uint32_t pos[8], val[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            pos[j] = lo + (uint32_t)(((uint64_t)n * (uint32_t)(j + 1)) / 9);
+            val[j] = __ldg(a + pos[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (val[j] < key) { c = j + 1; last_lt = pos[j] + 1; }
+        }
+        if (c < 8) first_ge = pos[c];
+        lo = last_lt;
+        hi = first_ge;            // a[first_ge] >= key, so the answer is <= first_ge
+        if (lo >= hi) return hi;
     }
-    return lo;
+    uint32_t below, equal;
+    count_short(a, lo, hi, key, below, equal);
+    return lo + below;
 }
 
 // Entries of predicate p in row r: [lo, lo + len) of S.idx. Rows are sorted
 // by (label, idx), so this is Eq. 8's S_p (x) A restricted to one row.
 __device__ __forceinline__ void label_range(const DStore& S, uint32_t r, uint32_t p, uint32_t& lo,
                                             uint32_t& len) {
-    uint32_t b = ld(S.ptr + r), e = ld(S.ptr + r + 1);
-    if (b == e || ld(S.lab + b) > p || ld(S.lab + e - 1) < p) { lo = b; len = 0; return; }
-    uint32_t l = lower_bound_u32(S.lab, b, e, p);
-    uint32_t h = lower_bound_u32(S.lab, l, e, p + 1);
-    lo = l; len = h - l;
+    const uint32_t b = ld(S.ptr + r), e = ld(S.ptr + r + 1);
+    if (e - b <= kShort) {
+        uint32_t below, equal;
+        count_short(S.lab, b, e, p, below, equal);
+        lo = b + below;
+        len = equal;
+        return;
+    }
+    const uint32_t l = lower_bound_u32(S.lab, b, e, p);
+    const uint32_t h = lower_bound_u32(S.lab, l, e, p + 1);
+    lo = l;
+    len = h - l;
 }
 
 // Does row r hold predicate p (Eq. 4 for one row)?
 __device__ __forceinline__ bool has_label(const DStore& S, uint32_t r, uint32_t p) {
-    uint32_t b = ld(S.ptr + r), e = ld(S.ptr + r + 1);
-    if (b == e || ld(S.lab + b) > p || ld(S.lab + e - 1) < p) return false;
-    uint32_t l = lower_bound_u32(S.lab, b, e, p);
+    const uint32_t b = ld(S.ptr + r), e = ld(S.ptr + r + 1);
+    if (e - b <= kShort) {
+        uint32_t below, equal;
+        count_short(S.lab, b, e, p, below, equal);
+        return equal != 0;
+    }
+    const uint32_t l = lower_bound_u32(S.lab, b, e, p);
     return l < e && ld(S.lab + l) == p;
 }
 
 // Is x in the sorted idx range [lo, lo + len)?
 __device__ __forceinline__ bool in_range(const DStore& S, uint32_t lo, uint32_t len, uint32_t x) {
     if (len == 0) return false;
-    uint32_t hi = lo + len;
-    if (ld(S.idx + lo) > x || ld(S.idx + hi - 1) < x) return false;
-    uint32_t k = lower_bound_u32(S.idx, lo, hi, x);
+    const uint32_t hi = lo + len;
+    if (len <= kShort) {
+        uint32_t below, equal;
+        count_short(S.idx, lo, hi, x, below, equal);
+        return equal != 0;
+    }
+    const uint32_t k = lower_bound_u32(S.idx, lo, hi, x);
     return k < hi && ld(S.idx + k) == x;
 }
 

@@ -28,69 +28,9 @@
 // a larger arena.
 #include <algorithm>
 
-#include "gs_device.cuh"
-#include "gs_exec.h"
+#include "gs_exec_dev.cuh"
 
 namespace gs {
-
-__host__ __device__ __forceinline__ uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
-
-__device__ __forceinline__ uint64_t level_off(const Ctl* c, int l) {
-    uint64_t o = kCtlBytes;
-    for (int j = 0; j < l; ++j) o += align256(8ull * c->n[j]);
-    return o;
-}
-
-// scratch for producing level l from np parent nodes with nbm binder slots
-__host__ __device__ __forceinline__ uint64_t scratch_bytes(uint64_t np, uint32_t nbm) {
-    return align256(8ull * np) + align256(8ull * np * nbm) + align256(np);
-}
-
-struct Scratch {
-    uint64_t* roff;
-    uint2* rng;
-    uint8_t* sel;
-    uint64_t base;
-};
-
-__device__ __forceinline__ Scratch scratch_at(const ExecDev& E, uint64_t np, uint32_t nbm) {
-    Scratch s;
-    uint64_t sb = scratch_bytes(np, nbm);
-    s.base = E.arena_bytes > sb ? E.arena_bytes - sb : 0;
-    s.roff = (uint64_t*)(E.arena + s.base);
-    s.rng = (uint2*)(E.arena + s.base + align256(8ull * np));
-    s.sel = (uint8_t*)(E.arena + s.base + align256(8ull * np) + align256(8ull * np * nbm));
-    return s;
-}
-
-__device__ __forceinline__ bool overflowed(const Ctl* c) {
-    return (*(volatile const uint32_t*)&c->status) & kStOverflow;
-}
-
-// Level base pointers in shared memory (computed once per block).
-__device__ __forceinline__ void load_levels(const ExecDev& E, int upto, const uint2** lv) {
-    if (threadIdx.x == 0) {
-        uint64_t o = kCtlBytes;
-        for (int j = 0; j <= upto && j < kMaxLevels; ++j) {
-            lv[j] = (const uint2*)(E.arena + o);
-            o += align256(8ull * E.ctl->n[j]);
-        }
-    }
-    __syncthreads();
-}
-
-// Bindings of levels 0..from of the node `idx` at level `from`.
-__device__ __forceinline__ void walk(const uint2* const* lv, int from, uint32_t idx, uint32_t* vid) {
-    for (int j = from; j >= 0; --j) {
-        uint2 e = lv[j][idx];
-        vid[j] = e.x;
-        idx = e.y;
-    }
-}
-
-__device__ __forceinline__ const DStore& store_of(const ExecDev& E, uint32_t dir) {
-    return dir == 0 ? E.out : E.in;
-}
 
 // ------------------------------------------------------------------ //
 
@@ -150,57 +90,6 @@ __global__ void __launch_bounds__(kThreads) k_range(ExecDev E, int l, LevelSpec 
     }
     sum = block_sum_u64(sum);
     if (threadIdx.x == 0) E.ctl->bsum[blockIdx.x] = sum;
-}
-
-// Candidate test of the pre-pruning step and of the other binders.
-__device__ __forceinline__ bool keep_candidate(const ExecDev& E, const LevelSpec& L, int l,
-                                               uint32_t x, const uint2* rng, uint32_t sel) {
-    if (L.use_bitmap) {
-        const uint32_t* bm = E.bits + (uint64_t)l * E.words;
-        if (!((__ldg(bm + (x >> 5)) >> (x & 31)) & 1u)) return false;
-    }
-    for (int b = 0; b < L.n_binders; ++b) {
-        if ((uint32_t)b == sel) continue;
-        uint2 r = rng[b];
-        if (!in_range(store_of(E, L.b[b].dir), r.x, r.y, x)) return false;
-    }
-    for (int j = 0; j < L.n_probes; ++j)
-        if (!has_label(store_of(E, L.pr[j].dir), x, L.pr[j].label)) return false;
-    for (int j = 0; j < L.n_self; ++j) {
-        uint32_t lo, len;
-        label_range(E.out, x, L.self_label[j], lo, len);
-        if (!in_range(E.out, lo, len, x)) return false;
-    }
-    return true;
-}
-
-// Warp-aggregated append of (x, parent) to a level with capacity cap.
-__device__ __forceinline__ void append(Ctl* ctl, int l, uint2* dst, uint64_t cap, bool keep,
-                                       uint32_t x, uint32_t parent) {
-    const uint32_t lane = lane_id();
-    uint32_t m = __ballot_sync(0xffffffffu, keep);
-    if (!m) return;
-    uint64_t base = 0;
-    uint32_t leader = __ffs(m) - 1;
-    if (lane == leader) base = atomicAdd((unsigned long long*)&ctl->n[l], (unsigned long long)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (keep) {
-        uint64_t pos = base + __popc(m & ((1u << lane) - 1u));
-        if (pos < cap) dst[pos] = make_uint2(x, parent);
-        else atomicOr(&ctl->status, kStOverflow);
-    }
-}
-
-constexpr int kExpItems = 8;                         // candidates per thread per tile
-constexpr uint64_t kExpTile = (uint64_t)kThreads * kExpItems;
-
-__device__ __forceinline__ uint64_t upper_bound_u64(const uint64_t* a, uint64_t lo, uint64_t hi,
-                                                    uint64_t key) {
-    while (lo < hi) {
-        uint64_t mid = lo + ((hi - lo) >> 1);
-        if (a[mid] <= key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
 }
 
 __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec L) {
@@ -270,26 +159,6 @@ __global__ void __launch_bounds__(kThreads) k_scan_apply_scratch(ExecDev E, cons
 
 // ------------------------------------------------------------------ //
 // Candidate vector -> ordered vertex list (warp ballot / popc + block scan).
-
-__device__ __forceinline__ bool self_ok(const ExecDev& E, const LevelSpec& L, uint32_t x) {
-    for (int j = 0; j < L.n_self; ++j) {
-        uint32_t lo, len;
-        label_range(E.out, x, L.self_label[j], lo, len);
-        if (!in_range(E.out, lo, len, x)) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ uint32_t word_keep(const ExecDev& E, const LevelSpec& L, uint32_t w,
-                                              uint32_t word) {
-    if (L.n_self == 0 || word == 0) return word;
-    uint32_t out = 0;
-    for (uint32_t m = word; m; m &= m - 1) {
-        uint32_t b = __ffs(m) - 1;
-        if (self_ok(E, L, w * 32 + b)) out |= 1u << b;
-    }
-    return out;
-}
 
 __global__ void __launch_bounds__(kThreads) k_bits_count(ExecDev E, int l, LevelSpec L) {
     if (overflowed(E.ctl)) return;

@@ -5,7 +5,8 @@
 
 namespace gs {
 
-constexpr uint32_t kStHuge = 4u;   // a tree node has more than 2^40 answer rows
+constexpr uint32_t kStHuge = 4u;      // a tree node has more than 2^40 answer rows
+constexpr uint32_t kStEscalate = 8u;  // the single-block kernel handed the query back
 
 // Control block at the start of the workspace: level sizes and the
 // partial sums of the device-wide scans. Zeroed before each evaluation.
@@ -46,7 +47,65 @@ struct EnumSpec {
     int32_t var_src[kMaxVars];
 };
 
+// The whole schedule of one query, passed by value to single-block kernels.
+struct QueryDev {
+    int32_t n_levels;
+    ConstChecks cc;
+    EnumSpec F;
+    LevelSpec lv[kMaxLevels];
+};
+
+inline void make_query_dev(const gs_plan* P, QueryDev* Q) {
+    Q->n_levels = P->n_levels;
+    Q->cc.n = (uint32_t)(P->const_triples.size() / 3);
+    if (Q->cc.n > (uint32_t)kMaxPatterns) Q->cc.n = kMaxPatterns;
+    for (uint32_t i = 0; i < 3 * Q->cc.n; ++i) Q->cc.t[i] = P->const_triples[i];
+    Q->F.n_leaves = P->n_leaves;
+    Q->F.n_vars = P->n_vars;
+    for (int j = 0; j < P->n_leaves; ++j) Q->F.leaf[j] = P->leaves[j];
+    for (int v = 0; v < P->n_vars; ++v) Q->F.var_src[v] = P->var_src[v];
+    for (int l = 0; l < P->n_levels; ++l) Q->lv[l] = P->levels[l];
+}
+
+// One query's answer in a batch: rows at pool + off, or escalated.
+struct BatchResult {
+    uint64_t off;
+    uint64_t rows;
+    uint32_t status;      // 0, or kStEscalate (run again on the grid path)
+    uint32_t pad;
+};
+
+// Parameters of the persistent batch kernel.
+struct BatchDev {
+    DStore out, in;
+    const uint8_t* recs;          // packed query records
+    const uint64_t* rec_off;      // byte offset of each record
+    uint32_t n;
+    uint8_t* slots;               // one workspace per CTA
+    uint64_t slot_bytes;
+    uint8_t* pool;                // answer rows of all queries
+    uint64_t pool_bytes;
+    unsigned long long* pool_top;
+    uint32_t* next;               // work counter
+    BatchResult* res;
+    uint64_t cand_budget, row_budget;
+};
+
+gs_status enqueue_batch(const BatchDev& B, int blocks, cudaStream_t st);
+int batch_blocks_per_sm();
+gs_status sort_rows_on_device(const gs_graph* g, const int32_t* rows, uint64_t n, uint32_t k,
+                              int32_t* out, cudaStream_t st);
+gs_status eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
+                          gs_result** out);
+// gs_eval_batch with at most max_blocks CTAs (0: one per resident slot) and a
+// pool of pool_bytes (0: the default).
+gs_status eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n, void* cuda_stream,
+                        int max_blocks, uint64_t pool_bytes, gs_batch** out);
+uint64_t batch_device_bytes(const gs_batch* b);
+
 uint64_t host_level_off(const uint64_t* n, int l);
+bool small_eligible(const gs_plan* P);
+gs_status enqueue_small(const gs_plan* P, const ExecDev& E, uint32_t* launches, cudaStream_t st);
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
                        cudaStream_t st);
 

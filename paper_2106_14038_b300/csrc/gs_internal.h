@@ -18,14 +18,16 @@ constexpr int kMaxLevels = 32;               // one materialized level per varia
 constexpr int kMaxBinders = 8;               // edges joining a level's variable to bound ends
 constexpr int kMaxProbes = 16;               // presence tests on a level's candidates
 constexpr int kMaxSelf = 8;                  // self-loop patterns ?w p ?w per variable
-constexpr int kMaxSlots = 31;                // distinct predicates per direction in one scan
+constexpr int kMaxSlots = 16;                // distinct predicates per direction in one scan
 constexpr int kBlocks = 1024;                // upper bound of the fixed grid (blocks)
 constexpr int kThreads = 256;
 
 // Rows whose degree exceeds kHeavyDeg are scanned in chunks of kHeavyChunk
-// entries, one warp per chunk, instead of one lane per row.
-constexpr uint32_t kHeavyDeg = 64;
-constexpr uint32_t kHeavyChunk = 2048;
+// entries, one warp per chunk, instead of inside their group of 32 rows.
+constexpr uint32_t kHeavyDeg = 8192;
+constexpr uint32_t kHeavyChunk = 16384;
+constexpr uint32_t kTileRows = 4096;      // rows per scan tile
+constexpr uint32_t kTileLabels = 8192;    // light labels per scan tile (+ one row)
 
 // Status bits written by kernels into the control block.
 constexpr uint32_t kStOverflow = 1u;  // a level or the output did not fit the workspace
@@ -63,6 +65,10 @@ struct Store {
     uint32_t* chunk_h = nullptr;    // [n_chunks] index into hrow
     uint32_t* chunk_start = nullptr;// [n_chunks] first entry of the chunk
     uint32_t n_heavy = 0, n_chunks = 0;
+    // scan tiles (x = first row, y = row count): runs of light rows, at most
+    // kTileRows rows and kTileLabels + kHeavyDeg labels; never a heavy row
+    uint2* tiles = nullptr;
+    uint32_t n_tiles = 0;
 };
 
 // Device view passed to kernels by value.

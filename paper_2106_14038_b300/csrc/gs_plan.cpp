@@ -297,7 +297,7 @@ gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t 
             bool w_is_subject = a == w;
             int other = w_is_subject ? b : a;
             int64_t other_const = w_is_subject ? o : s;
-            bool bound = other < 0 || level_of[other] >= 0 && level_of[other] < l;
+            bool bound = other < 0 || (level_of[other] >= 0 && level_of[other] < l);
             if (bound) {
                 bool dup = false;
                 for (int j = 0; j < L.n_binders; ++j) {

@@ -1,0 +1,319 @@
+// Serving loop: continuous batching of submitted queries over the resident
+// graph. A worker thread owns the device work:
+//   - admission: queued plans are taken in arrival order into a batch while
+//     the batch's device memory estimate (per-CTA workspace slots plus an
+//     answer pool) fits under the server's budget together with everything
+//     in flight, and while a stream is free;
+//   - launch: the batch runs on its own stream (gs_eval_batch's persistent
+//     kernel), so batches admitted while others are running overlap on the
+//     device;
+//   - completion: in-flight batches are polled with events; a finished
+//     batch completes its tickets (answers stay on the device until the
+//     ticket is released) and returns its memory to the budget.
+// Callers submit and poll from their own threads; everything shared is
+// under one mutex, and CUDA work for one batch is only issued by the worker.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gs_exec.h"
+
+using namespace gs;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Flight {
+    gs_batch* b = nullptr;
+    int stream = -1;
+    uint64_t bytes = 0;
+    std::vector<uint64_t> tickets;
+    std::vector<const gs_plan*> plans;
+    int refs = 0;                 // tickets not yet released
+};
+
+struct Ticket {
+    const gs_plan* plan = nullptr;
+    Clock::time_point submitted, done_at;
+    int state = 0;                // 0 queued, 1 running, 2 done, 3 failed
+    std::shared_ptr<Flight> flight;
+    uint32_t index = 0;
+    uint64_t rows = 0;
+    gs_status err = GS_OK;
+};
+
+}  // namespace
+
+struct gs_server {
+    gs_graph* g = nullptr;
+    gs_server_config cfg{};
+    std::vector<cudaStream_t> streams;
+    std::vector<char> stream_busy;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stopping = false;
+    std::thread worker;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, Ticket> tickets;
+    std::vector<std::shared_ptr<Flight>> inflight;
+    uint64_t next_id = 1;
+    uint64_t inflight_bytes = 0, peak_bytes = 0;
+    uint64_t completed = 0, batches = 0;
+    gs_status fatal = GS_OK;
+};
+
+namespace {
+
+// Device bytes a batch of n queries will hold while it runs.
+uint64_t estimate(const gs_server* s, uint32_t n) {
+    const uint64_t slots = std::min<uint64_t>(n, (uint64_t)s->g->sm_count * batch_blocks_per_sm());
+    return slots * (24ull << 20) + (uint64_t)n * s->cfg.pool_bytes_per_query;
+}
+
+void complete(gs_server* s, std::shared_ptr<Flight>& f) {
+    // called without the lock: may wait for queries handed to the grid path
+    std::vector<uint64_t> rows(f->tickets.size(), 0);
+    gs_status rc = gs_batch_info(f->b, rows.data(), nullptr);
+    std::lock_guard<std::mutex> lk(s->mu);
+    const auto now = Clock::now();
+    for (size_t i = 0; i < f->tickets.size(); ++i) {
+        auto it = s->tickets.find(f->tickets[i]);
+        if (it == s->tickets.end()) continue;
+        it->second.state = rc == GS_OK ? 2 : 3;
+        it->second.err = rc;
+        it->second.rows = rows[i];
+        it->second.done_at = now;
+    }
+    s->stream_busy[f->stream] = 0;
+    s->completed += f->tickets.size();
+}
+
+void worker_loop(gs_server* s) {
+    cudaSetDevice(s->g->device);
+    for (;;) {
+        std::vector<std::shared_ptr<Flight>> finished;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->queue.empty() && s->inflight.empty())
+                s->cv.wait_for(lk, std::chrono::microseconds(s->cfg.max_wait_us));
+            if (s->stopping && s->queue.empty() && s->inflight.empty()) break;
+            // completions
+            for (size_t i = 0; i < s->inflight.size();) {
+                int done = 0;
+                gs_batch_poll(s->inflight[i]->b, &done);
+                if (done) {
+                    finished.push_back(s->inflight[i]);
+                    s->inflight.erase(s->inflight.begin() + i);
+                } else {
+                    ++i;
+                }
+            }
+            // admission
+            while (!s->queue.empty()) {
+                int st = -1;
+                for (size_t k = 0; k < s->streams.size(); ++k)
+                    if (!s->stream_busy[k]) { st = (int)k; break; }
+                if (st < 0) break;
+                uint32_t take = 0;
+                uint64_t bytes = 0;
+                while (take < s->queue.size() && take < s->cfg.max_batch) {
+                    uint64_t b2 = estimate(s, take + 1);
+                    if (s->inflight_bytes + b2 > s->cfg.memory_budget && take > 0) break;
+                    bytes = b2;
+                    ++take;
+                }
+                if (take == 0 || (s->inflight_bytes + bytes > s->cfg.memory_budget && !s->inflight.empty()))
+                    break;   // wait for memory to free up
+                auto f = std::make_shared<Flight>();
+                f->stream = st;
+                f->bytes = bytes;
+                for (uint32_t i = 0; i < take; ++i) {
+                    uint64_t id = s->queue.front();
+                    s->queue.pop_front();
+                    Ticket& t = s->tickets[id];
+                    t.state = 1;
+                    t.flight = f;
+                    t.index = i;
+                    f->tickets.push_back(id);
+                    f->plans.push_back(t.plan);
+                }
+                f->refs = (int)take;
+                gs_status rc = eval_batch_ex(s->g, f->plans.data(), take, (void*)s->streams[st],
+                                             0, s->cfg.pool_bytes_per_query * take, &f->b);
+                if (rc != GS_OK) {
+                    for (uint64_t id : f->tickets) {
+                        Ticket& t = s->tickets[id];
+                        t.state = 3;
+                        t.err = rc;
+                        t.done_at = Clock::now();
+                    }
+                    continue;
+                }
+                s->stream_busy[st] = 1;
+                s->inflight_bytes += bytes;
+                s->peak_bytes = std::max(s->peak_bytes, s->inflight_bytes);
+                s->inflight.push_back(f);
+                s->batches++;
+            }
+        }
+        for (auto& f : finished) {
+            complete(s, f);
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->inflight_bytes -= f->bytes;
+        }
+        if (finished.empty()) {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (!s->inflight.empty() && s->queue.empty())
+                s->cv.wait_for(lk, std::chrono::microseconds(20));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_server_start(gs_graph* g, const gs_server_config* cfg, gs_server** out) {
+    if (!g || !out) { set_error("gs_server_start: NULL argument"); return GS_EINVAL; }
+    *out = nullptr;
+    gs_server* s = new (std::nothrow) gs_server();
+    if (!s) { set_error("gs_server_start: host out of memory"); return GS_ENOMEM; }
+    s->g = g;
+    gs_server_config c{};
+    c.max_batch = 1024;
+    c.n_streams = 4;
+    c.memory_budget = 40ull << 30;
+    c.max_wait_us = 50;
+    c.pool_bytes_per_query = 16ull << 20;
+    if (cfg) {
+        if (cfg->max_batch) c.max_batch = cfg->max_batch;
+        if (cfg->n_streams) c.n_streams = cfg->n_streams;
+        if (cfg->memory_budget) c.memory_budget = cfg->memory_budget;
+        if (cfg->max_wait_us) c.max_wait_us = cfg->max_wait_us;
+        if (cfg->pool_bytes_per_query) c.pool_bytes_per_query = cfg->pool_bytes_per_query;
+    }
+    s->cfg = c;
+    for (uint32_t i = 0; i < c.n_streams; ++i) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            gs_status rc = cuda_fail(cudaGetLastError(), "gs_server_start");
+            for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+            delete s;
+            return rc;
+        }
+        s->streams.push_back(st);
+    }
+    s->stream_busy.assign(c.n_streams, 0);
+    s->worker = std::thread(worker_loop, s);
+    *out = s;
+    return GS_OK;
+}
+
+gs_status gs_server_submit(gs_server* s, const gs_plan* plan, uint64_t* ticket) {
+    if (!s || !plan || !ticket) { set_error("gs_server_submit: NULL argument"); return GS_EINVAL; }
+    if (plan->N != 0 && (plan->N != s->g->N || plan->P != s->g->P)) {
+        set_error("gs_server_submit: the plan was made for another graph");
+        return GS_EINVAL;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stopping) { set_error("gs_server_submit: the server is stopping"); return GS_EINVAL; }
+        uint64_t id = s->next_id++;
+        Ticket& t = s->tickets[id];
+        t.plan = plan;
+        t.submitted = Clock::now();
+        s->queue.push_back(id);
+        *ticket = id;
+    }
+    s->cv.notify_one();
+    return GS_OK;
+}
+
+gs_status gs_server_poll(gs_server* s, uint64_t ticket, int* done, uint64_t* rows,
+                         double* latency_us) {
+    if (!s || !done) { set_error("gs_server_poll: NULL argument"); return GS_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) { set_error("gs_server_poll: unknown ticket %llu", (unsigned long long)ticket); return GS_EINVAL; }
+    const Ticket& t = it->second;
+    if (t.state == 3) { set_error("gs_server_poll: the query failed"); *done = 1; return t.err; }
+    *done = t.state == 2;
+    if (*done) {
+        if (rows) *rows = t.rows;
+        if (latency_us)
+            *latency_us = std::chrono::duration<double, std::micro>(t.done_at - t.submitted).count();
+    }
+    return GS_OK;
+}
+
+gs_status gs_server_fetch(gs_server* s, uint64_t ticket, int32_t* dst, uint64_t cap_rows,
+                          int dst_on_device, int sort_rows) {
+    if (!s) { set_error("gs_server_fetch: NULL argument"); return GS_EINVAL; }
+    std::shared_ptr<Flight> f;
+    uint32_t index = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->tickets.find(ticket);
+        if (it == s->tickets.end() || it->second.state != 2) {
+            set_error("gs_server_fetch: ticket %llu is not finished", (unsigned long long)ticket);
+            return GS_EINVAL;
+        }
+        f = it->second.flight;
+        index = it->second.index;
+    }
+    return gs_batch_fetch(f->b, index, dst, cap_rows, dst_on_device, sort_rows);
+}
+
+gs_status gs_server_release(gs_server* s, uint64_t ticket) {
+    if (!s) { set_error("gs_server_release: NULL argument"); return GS_EINVAL; }
+    std::shared_ptr<Flight> f;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->tickets.find(ticket);
+        if (it == s->tickets.end()) { set_error("gs_server_release: unknown ticket"); return GS_EINVAL; }
+        if (it->second.state < 2) { set_error("gs_server_release: ticket still running"); return GS_EINVAL; }
+        f = it->second.flight;
+        s->tickets.erase(it);
+        if (f && --f->refs > 0) f.reset();
+    }
+    if (f) gs_free_batch(f->b);   // last ticket of its batch
+    return GS_OK;
+}
+
+gs_status gs_server_stats(gs_server* s, uint64_t* completed, uint64_t* batches,
+                          uint64_t* peak_bytes) {
+    if (!s) { set_error("gs_server_stats: NULL argument"); return GS_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (completed) *completed = s->completed;
+    if (batches) *batches = s->batches;
+    if (peak_bytes) *peak_bytes = s->peak_bytes;
+    return GS_OK;
+}
+
+void gs_server_stop(gs_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    std::vector<gs_batch*> left;
+    for (auto& kv : s->tickets)
+        if (kv.second.flight && kv.second.flight->b) left.push_back(kv.second.flight->b);
+    std::sort(left.begin(), left.end());
+    left.erase(std::unique(left.begin(), left.end()), left.end());
+    for (gs_batch* b : left) gs_free_batch(b);
+    for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    delete s;
+}
+
+}  // extern "C"

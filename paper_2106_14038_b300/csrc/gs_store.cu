@@ -241,6 +241,54 @@ __global__ void k_heavy_write(const uint32_t* __restrict__ ptr, uint32_t N,
     }
 }
 
+// Scan tiles: runs of consecutive light rows (degree <= kHeavyDeg) cut
+// every kTileLabels light labels, every kTileRows rows and at every heavy
+// row. With pre[r] = (heavy rows before r) << 40 | (light labels before r),
+// a light row's tile key is (heavy rows before, light labels / kTileLabels,
+// r / kTileRows); a tile is a maximal run of light rows with one key, so it
+// holds at most kTileRows rows and kTileLabels + kHeavyDeg labels.
+constexpr uint64_t kLow40 = (1ull << 40) - 1;
+
+__device__ __forceinline__ uint64_t tile_key(uint64_t pre, uint32_t r) {
+    return ((pre >> 40) << 40) | ((uint64_t)(r / kTileRows) << 20) | ((pre & kLow40) / kTileLabels);
+}
+
+__global__ void k_tile_prep(const uint32_t* __restrict__ ptr, uint32_t N, uint64_t* __restrict__ val) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t d = ptr[r + 1] - ptr[r];
+        val[r] = d > kHeavyDeg ? (1ull << 40) : (uint64_t)d;
+    }
+}
+
+__device__ __forceinline__ bool tile_start(const uint32_t* __restrict__ ptr,
+                                           const uint64_t* __restrict__ pre, uint32_t r) {
+    if (ptr[r + 1] - ptr[r] > kHeavyDeg) return false;
+    if (r == 0) return true;
+    if (ptr[r] - ptr[r - 1] > kHeavyDeg) return true;
+    return tile_key(pre[r], r) != tile_key(pre[r - 1], r - 1);
+}
+
+__global__ void k_tile_flags(const uint32_t* __restrict__ ptr, uint32_t N,
+                             const uint64_t* __restrict__ pre, uint64_t* __restrict__ flg) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
+         r += (uint64_t)gridDim.x * blockDim.x)
+        flg[r] = tile_start(ptr, pre, (uint32_t)r) ? 1ull : 0ull;
+}
+
+__global__ void k_tile_write(const uint32_t* __restrict__ ptr, uint32_t N,
+                             const uint64_t* __restrict__ pre, const uint64_t* __restrict__ tix,
+                             uint2* __restrict__ tiles) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        if (!tile_start(ptr, pre, (uint32_t)r)) continue;
+        const uint64_t key = tile_key(pre[r], (uint32_t)r);
+        uint32_t e = (uint32_t)r + 1;
+        while (e < N && ptr[e + 1] - ptr[e] <= kHeavyDeg && tile_key(pre[e], e) == key) ++e;
+        tiles[tix[r]] = make_uint2((uint32_t)r, e - (uint32_t)r);
+    }
+}
+
 static gs_status build_dir(gs_graph* g, const uint32_t* s, const uint32_t* p, const uint32_t* o,
                            uint64_t n, int by_col, int vb, int lb, uint64_t* k0, uint64_t* k1,
                            uint64_t* misc, Store& S, cudaStream_t st) {
@@ -309,8 +357,50 @@ static gs_status build_dir(gs_graph* g, const uint32_t* s, const uint32_t* p, co
     S.hrow = (uint32_t*)g->alloc.get(sizeof(uint32_t) * (S.n_heavy + 1), st);
     S.chunk_h = (uint32_t*)g->alloc.get(sizeof(uint32_t) * (S.n_chunks + 1), st);
     S.chunk_start = (uint32_t*)g->alloc.get(sizeof(uint32_t) * (S.n_chunks + 1), st);
-    if (!S.hrow || !S.chunk_h || !S.chunk_start) { set_error("gs_load_triples: out of device memory"); return GS_ENOMEM; }
+    if (!S.hrow || !S.chunk_h || !S.chunk_start) {
+        if (own_cnt) g->alloc.put(cnt, st);
+        set_error("gs_load_triples: out of device memory");
+        return GS_ENOMEM;
+    }
     k_heavy_write<<<nb, kThreads, 0, st>>>(S.ptr, g->N, cnt, S.hrow, S.chunk_h, S.chunk_start);
+    GS_CUDA(cudaGetLastError());
+    GS_CUDA(cudaStreamSynchronize(st));
+
+    // scan tiles: pre = prefix of (heavy << 40 | light degree), flags, their prefix
+    uint64_t* flg = keys;   // the sorted keys are no longer needed
+    bool own_flg = false;
+    if (n < (uint64_t)g->N + 1) {
+        flg = (uint64_t*)g->alloc.get(sizeof(uint64_t) * ((uint64_t)g->N + 1), st);
+        if (!flg) {
+            if (own_cnt) g->alloc.put(cnt, st);
+            set_error("gs_load_triples: out of device memory");
+            return GS_ENOMEM;
+        }
+        own_flg = true;
+    }
+    k_tile_prep<<<nb, kThreads, 0, st>>>(S.ptr, g->N, cnt);
+    k_block_sums_u64<<<nb, kThreads, 0, st>>>(cnt, n_dev, bsum, nullptr);
+    k_scan_block_sums<<<1, kThreads, 0, st>>>(bsum, boff, nb, tot, nullptr);
+    k_scan_apply_u64<<<nb, kThreads, 0, st>>>(cnt, n_dev, boff, nullptr);
+    k_tile_flags<<<nb, kThreads, 0, st>>>(S.ptr, g->N, cnt, flg);
+    k_block_sums_u64<<<nb, kThreads, 0, st>>>(flg, n_dev, bsum, nullptr);
+    k_scan_block_sums<<<1, kThreads, 0, st>>>(bsum, boff, nb, tot, nullptr);
+    k_scan_apply_u64<<<nb, kThreads, 0, st>>>(flg, n_dev, boff, nullptr);
+    uint64_t nt = 0;
+    GS_CUDA(cudaMemcpyAsync(&nt, tot, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    S.n_tiles = (uint32_t)nt;
+    S.tiles = (uint2*)g->alloc.get(sizeof(uint2) * (nt + 1), st);
+    if (!S.tiles) {
+        if (own_cnt) g->alloc.put(cnt, st);
+        if (own_flg) g->alloc.put(flg, st);
+        set_error("gs_load_triples: out of device memory");
+        return GS_ENOMEM;
+    }
+    k_tile_write<<<nb, kThreads, 0, st>>>(S.ptr, g->N, cnt, flg, S.tiles);
+    GS_CUDA(cudaGetLastError());
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (own_flg) g->alloc.put(flg, st);
     GS_CUDA(cudaGetLastError());
     GS_CUDA(cudaStreamSynchronize(st));
     if (own_cnt) g->alloc.put(cnt, st);
@@ -358,6 +448,7 @@ void free_store(gs_graph* g, cudaStream_t st) {
     for (Store* S : {&g->out, &g->in}) {
         g->alloc.put(S->ptr, st); g->alloc.put(S->idx, st); g->alloc.put(S->lab, st);
         g->alloc.put(S->hrow, st); g->alloc.put(S->chunk_h, st); g->alloc.put(S->chunk_start, st);
+        g->alloc.put(S->tiles, st);
         *S = Store{};
     }
 }

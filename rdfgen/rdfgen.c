@@ -282,95 +282,147 @@ int rdfgen_embed(const rdf_adj* g, uint32_t n_sv, uint32_t n_se, const uint32_t*
     free(mv);
     return ok ? 0 : 1;
 }
-
 /* Upper bound on the number of matches of a query: the exact match count
  * of its spanning tree (first n_sv-1 shape edges of the embedding order,
  * non-tree edges dropped), counting raw triples with multiplicity.
  *   n_sv, se    the shape used for the embedding (tree edges first)
  *   is_const, mapped, u_subject  as returned by rdfgen_embed
  *   patterns    n_se x 3, from rdfgen_embed
- * Vectors whose support is small (subtrees that hold a constant) are
- * propagated through the adjacency of their support; the others through
- * the predicate's whole triple list. Returns the bound as a double. */
+ * A tree DP: f_u(x) = prod over children w of sum_{y joined to x by the
+ * child's edge} f_w(y). Children whose vector has a small support (their
+ * subtree holds a constant) are folded first through the adjacency of that
+ * support; later children are then evaluated only where the parent is
+ * still non-zero. Only when both sides are dense does a fold read the
+ * predicate's whole triple list. Returns the bound as a double. */
+
+typedef struct { double* v; uint32_t* sup; uint64_t nsup; int sparse; } dvec;
+
+static void dvec_support(dvec* d, uint32_t N, uint64_t small) {
+    uint64_t nz = 0;
+    for (uint32_t x = 0; x < N; ++x) nz += d->v[x] != 0.0;
+    d->sparse = nz < small;
+    d->nsup = 0;
+    if (d->sparse) {
+        d->sup = (uint32_t*)realloc(d->sup, sizeof(uint32_t) * (nz ? nz : 1));
+        for (uint32_t x = 0; x < N; ++x) if (d->v[x] != 0.0) d->sup[d->nsup++] = x;
+    }
+}
+
 double rdfgen_tree_bound(const rdf_adj* g, uint32_t n_sv, const uint32_t* se,
                          const uint8_t* is_const, const uint32_t* mapped, const int64_t* patterns,
                          const uint8_t* u_subject) {
     const uint32_t N = g->n_vertices;
     const uint64_t small = N / 16 + 1;
-    double** f = (double**)calloc(n_sv, sizeof(double*));
-    uint32_t** sup = (uint32_t**)calloc(n_sv, sizeof(uint32_t*));   /* NULL = dense */
-    uint64_t* nsup = (uint64_t*)calloc(n_sv, sizeof(uint64_t));
+    dvec* f = (dvec*)calloc(n_sv, sizeof(dvec));
     double* tmp = (double*)malloc(sizeof(double) * N);
-    for (uint32_t v = 0; v < n_sv; ++v) {
-        f[v] = (double*)malloc(sizeof(double) * N);
-        if (is_const[v]) {
-            memset(f[v], 0, sizeof(double) * N); f[v][mapped[v]] = 1.0;
-            sup[v] = (uint32_t*)malloc(sizeof(uint32_t)); sup[v][0] = mapped[v]; nsup[v] = 1;
+    /* parent edge of every shape vertex (tree edges only) */
+    int64_t* pe = (int64_t*)malloc(sizeof(int64_t) * n_sv);
+    for (uint32_t v = 0; v < n_sv; ++v) pe[v] = -1;
+    for (uint32_t e = 0; e + 1 < n_sv; ++e) pe[se[2 * e + 1]] = e;
+    /* discovery order: vertex 0, then the child of each tree edge in order */
+    uint32_t* order = (uint32_t*)malloc(sizeof(uint32_t) * n_sv);
+    order[0] = 0;
+    for (uint32_t e = 0; e + 1 < n_sv; ++e) order[e + 1] = se[2 * e + 1];
+    for (int64_t oi = (int64_t)n_sv - 1; oi >= 0; --oi) {
+        uint32_t u = order[oi];
+        dvec* fu = &f[u];
+        fu->v = (double*)malloc(sizeof(double) * N);
+        if (is_const[u]) {
+            memset(fu->v, 0, sizeof(double) * N);
+            fu->v[mapped[u]] = 1.0;
+            fu->sup = (uint32_t*)malloc(sizeof(uint32_t));
+            fu->sup[0] = mapped[u]; fu->nsup = 1; fu->sparse = 1;
         } else {
-            for (uint32_t x = 0; x < N; ++x) f[v][x] = 1.0;
+            for (uint32_t x = 0; x < N; ++x) fu->v[x] = 1.0;
+            fu->sparse = 0;
         }
-    }
-    for (int64_t e = (int64_t)n_sv - 2; e >= 0; --e) {
-        uint32_t u = se[2 * e], w = se[2 * e + 1];     /* u parent, w child */
-        uint32_t p = (uint32_t)patterns[3 * e + 1];
-        int us = u_subject[e];
-        memset(tmp, 0, sizeof(double) * N);
-        if (sup[w]) {
-            for (uint64_t k = 0; k < nsup[w]; ++k) {
-                uint32_t y = sup[w][k];
-                /* triples joining y to some x with label p, y on the w side */
-                const uint64_t* off = us ? g->in_off : g->out_off;
-                const uint64_t* ix = us ? g->in_idx : g->out_idx;
-                for (uint64_t t = off[y]; t < off[y + 1]; ++t) {
-                    uint64_t ti = ix[t];
-                    if (g->p[ti] != p) continue;
-                    uint32_t x = us ? g->s[ti] : g->o[ti];
-                    tmp[x] += f[w][y];
+        /* children of u, sparse ones first */
+        for (int pass = 0; pass < 2; ++pass) {
+            for (uint32_t e = 0; e + 1 < n_sv; ++e) {
+                if (se[2 * e] != u) continue;
+                uint32_t w = se[2 * e + 1];
+                dvec* fw = &f[w];
+                if ((pass == 0) != (fw->sparse != 0)) continue;
+                uint32_t p = (uint32_t)patterns[3 * e + 1];
+                int us = u_subject[e];
+                /* x is u's end, y is w's end of a triple with label p */
+                const uint64_t* xoff = us ? g->out_off : g->in_off;
+                const uint64_t* xix = us ? g->out_idx : g->in_idx;
+                const uint64_t* yoff = us ? g->in_off : g->out_off;
+                const uint64_t* yix = us ? g->in_idx : g->out_idx;
+                if (fu->sparse) {
+                    /* evaluate only where f_u is non-zero, through x's adjacency */
+                    uint64_t keep = 0;
+                    for (uint64_t k = 0; k < fu->nsup; ++k) {
+                        uint32_t x = fu->sup[k];
+                        double acc = 0.0;
+                        for (uint64_t t = xoff[x]; t < xoff[x + 1]; ++t) {
+                            uint64_t ti = xix[t];
+                            if (g->p[ti] != p) continue;
+                            acc += fw->v[us ? g->o[ti] : g->s[ti]];
+                        }
+                        fu->v[x] *= acc;
+                        if (fu->v[x] != 0.0) fu->sup[keep++] = x;
+                    }
+                    fu->nsup = keep;
+                } else if (fw->sparse) {
+                    memset(tmp, 0, sizeof(double) * N);
+                    for (uint64_t k = 0; k < fw->nsup; ++k) {
+                        uint32_t y = fw->sup[k];
+                        for (uint64_t t = yoff[y]; t < yoff[y + 1]; ++t) {
+                            uint64_t ti = yix[t];
+                            if (g->p[ti] != p) continue;
+                            tmp[us ? g->s[ti] : g->o[ti]] += fw->v[y];
+                        }
+                    }
+                    for (uint32_t x = 0; x < N; ++x) fu->v[x] *= tmp[x];
+                    dvec_support(fu, N, small);
+                } else {
+                    int nt = 1;
+#ifdef _OPENMP
+                    nt = omp_get_max_threads();
+#endif
+                    double* part = (double*)calloc((size_t)nt * N, sizeof(double));
+                    const uint64_t b0 = g->pred_off[p], b1 = g->pred_off[p + 1];
+                    const double* wv = fw->v;
+                    double* uv = fu->v;
+                    #pragma omp parallel num_threads(nt)
+                    {
+                        int tid = 0;
+#ifdef _OPENMP
+                        tid = omp_get_thread_num();
+#endif
+                        double* mine = part + (size_t)tid * N;
+                        #pragma omp for schedule(static)
+                        for (int64_t t = (int64_t)b0; t < (int64_t)b1; ++t) {
+                            uint64_t ti = g->pred_idx[t];
+                            uint32_t x = us ? g->s[ti] : g->o[ti];
+                            uint32_t y = us ? g->o[ti] : g->s[ti];
+                            mine[x] += wv[y];
+                        }
+                        #pragma omp for schedule(static)
+                        for (int64_t x = 0; x < (int64_t)N; ++x) {
+                            double acc = 0.0;
+                            for (int k = 0; k < nt; ++k) acc += part[(size_t)k * N + x];
+                            uv[x] *= acc;
+                        }
+                    }
+                    free(part);
+                    dvec_support(fu, N, small);
                 }
             }
-        } else {
-            /* per-thread partial sums, then a reduction over x */
-            int nt = 1;
-#ifdef _OPENMP
-            nt = omp_get_max_threads();
-#endif
-            double* part = (double*)calloc((size_t)nt * N, sizeof(double));
-            const uint64_t b0 = g->pred_off[p], b1 = g->pred_off[p + 1];
-            const double* fw = f[w];
-            #pragma omp parallel num_threads(nt)
-            {
-                int tid = 0;
-#ifdef _OPENMP
-                tid = omp_get_thread_num();
-#endif
-                double* mine = part + (size_t)tid * N;
-                #pragma omp for schedule(static)
-                for (int64_t t = (int64_t)b0; t < (int64_t)b1; ++t) {
-                    uint64_t ti = g->pred_idx[t];
-                    uint32_t x = us ? g->s[ti] : g->o[ti];
-                    uint32_t y = us ? g->o[ti] : g->s[ti];
-                    mine[x] += fw[y];
-                }
-                #pragma omp for schedule(static)
-                for (int64_t x = 0; x < (int64_t)N; ++x) {
-                    double acc = 0.0;
-                    for (int k = 0; k < nt; ++k) acc += part[(size_t)k * N + x];
-                    tmp[x] = acc;
-                }
-            }
-            free(part);
         }
-        uint64_t nz = 0;
-        for (uint32_t x = 0; x < N; ++x) { f[u][x] *= tmp[x]; nz += f[u][x] != 0.0; }
-        free(sup[u]); sup[u] = NULL; nsup[u] = 0;
-        if (nz < small) {
-            sup[u] = (uint32_t*)malloc(sizeof(uint32_t) * (nz ? nz : 1));
-            for (uint32_t x = 0; x < N; ++x) if (f[u][x] != 0.0) sup[u][nsup[u]++] = x;
+        /* children are no longer needed */
+        for (uint32_t e = 0; e + 1 < n_sv; ++e) {
+            if (se[2 * e] != u) continue;
+            uint32_t w = se[2 * e + 1];
+            free(f[w].v); free(f[w].sup); f[w].v = NULL; f[w].sup = NULL;
         }
     }
     double total = 0.0;
-    for (uint32_t x = 0; x < N; ++x) total += f[0][x];
-    for (uint32_t v = 0; v < n_sv; ++v) { free(f[v]); free(sup[v]); }
-    free(f); free(sup); free(nsup); free(tmp);
+    if (f[0].sparse) for (uint64_t k = 0; k < f[0].nsup; ++k) total += f[0].v[f[0].sup[k]];
+    else for (uint32_t x = 0; x < N; ++x) total += f[0].v[x];
+    free(f[0].v); free(f[0].sup);
+    free(f); free(tmp); free(pe); free(order);
     return total;
 }

@@ -14,6 +14,14 @@ import rdfgen
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(params=["auto", "grid"])
+def exec_path(request, monkeypatch):
+    """auto: single-block kernel for plans without a full scan (escalating
+    to the grid path when a level is large); grid: always the grid path."""
+    monkeypatch.setenv("GS_EXEC", request.param)
+    return request.param
+
+
 def _graph(s, p, o, nv, npred):
     return gs.Graph(s, p, o, nv, npred), oracle.Index(s, p, o, nv, npred)
 
@@ -137,7 +145,7 @@ def _same(g, ix, pats, flags=0):
 
 
 @pytest.mark.parametrize("block", range(4))
-def test_eval_random_tiny_cases(block):
+def test_eval_random_tiny_cases(block, exec_path):
     # the oracle is pinned to exhaustive enumeration on exactly these cases
     for seed in range(block * 60, block * 60 + 60):
         nv = 3 + seed % 5
@@ -149,7 +157,7 @@ def test_eval_random_tiny_cases(block):
         _same(g, ix, q, flags=gs.PLAN_DIRECTION)
 
 
-def test_eval_rmat14_workload(rmat14):
+def test_eval_rmat14_workload(rmat14, exec_path):
     w, (s, p, o), g, ix = rmat14
     sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
     for q in rdfgen.queries(w, sm):
@@ -157,7 +165,7 @@ def test_eval_rmat14_workload(rmat14):
         assert len(rows) >= 1     # the embedding that produced the query matches
 
 
-def test_eval_mid_size_random_shapes():
+def test_eval_mid_size_random_shapes(exec_path):
     w = rdfgen.Workload("t", 12, 40000, 8, 1.0, 4242, 0, 0, 0)
     s, p, o = rdfgen.graph(w)
     g, ix = _graph(s, p, o, w.n_vertices, w.n_preds)
@@ -173,7 +181,7 @@ def test_eval_mid_size_random_shapes():
     assert n == 27
 
 
-def test_eval_edge_cases(rmat14):
+def test_eval_edge_cases(rmat14, exec_path):
     w, (s, p, o), g, ix = rmat14
     t0 = (int(s[0]), int(p[0]), int(o[0]))
     # exactly one row: an (s, p) pair with a single object
@@ -224,7 +232,7 @@ def test_fetch_unsorted_is_a_permutation_and_overflow(rmat14):
     r.close()
 
 
-def test_workspace_retry(rmat14, monkeypatch):
+def test_workspace_retry(rmat14, monkeypatch, exec_path):
     # a tiny first workspace forces the overflow -> grow -> re-run path
     w, _, g, ix = rmat14
     monkeypatch.setenv("GS_ARENA_BYTES", "65536")
@@ -233,14 +241,118 @@ def test_workspace_retry(rmat14, monkeypatch):
         _same(g, ix, pats)
 
 
-def test_hub_graph_expansion():
-    # one hub with 60000 out-edges: load-balanced expansion over a huge range
+def test_hub_graph_expansion(exec_path):
+    # one hub with 80000 out-edges: load-balanced expansion over a huge range;
+    # through the constant it also exceeds the single-block budget (escalation)
     rng = np.random.default_rng(9)
-    n_v = 70000
-    s = np.concatenate([np.zeros(60000, np.int64), rng.integers(0, n_v, 60000)])
-    o = np.concatenate([np.arange(1, 60001), rng.integers(0, n_v, 60000)])
-    p = np.concatenate([np.ones(60000, np.int64), rng.integers(1, 4, 60000)])
+    n_v = 90000
+    s = np.concatenate([np.zeros(80000, np.int64), rng.integers(0, n_v, 60000)])
+    o = np.concatenate([np.arange(1, 80001), rng.integers(0, n_v, 60000)])
+    p = np.concatenate([np.ones(80000, np.int64), rng.integers(1, 4, 60000)])
     g, ix = _graph(s, p, o, n_v, 3)
     _same(g, ix, [(0, 1, -1), (-1, 2, -2)])
+    _same(g, ix, [(0, 1, -1)])
+    _same(g, ix, [(0, 1, -1), (-1, 2, -2), (-2, 3, -3)])
     _same(g, ix, [(-1, 1, -2), (-2, 2, -3)])
     _same(g, ix, [(-1, 1, -2), (-1, 1, -3), (-2, 3, -3)])
+
+
+def test_batch_equals_oracle(rmat14, monkeypatch):
+    # one persistent launch over many queries of every shape, including
+    # constant-free ones (grid path) and ones that outgrow one CTA
+    w, (s, p, o), g, ix = rmat14
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    pats = [q.patterns for q in rdfgen.queries(w, sm)]
+    rng = np.random.default_rng(4)
+    for i in range(40):
+        sh = [rdfgen.star(2), rdfgen.chain(2), rdfgen.cycle(3), rdfgen.snowflake([1, 1])][i % 4]
+        sh.const = [int(rng.integers(0, sh.n_v))]
+        q = sm.sample(sh, 99, i, 1e5)
+        pats.append(q.patterns)
+    pats.append(np.array([(-1, 1, -2)], np.int64))        # large: grid path
+    b = g.eval_batch(pats)
+    rows = b.rows()
+    ms, launches, esc = b.stats()
+    assert launches >= 1
+    for i, pt in enumerate(pats):
+        want = ix.eval(pt, threads=4)
+        assert int(rows[i]) == len(want), i
+        assert np.array_equal(b.fetch(i), want), i
+    b.close()
+
+
+def test_batch_small_pool_hands_back(rmat14, monkeypatch):
+    # a pool too small for most answers: those queries go to the grid path
+    w, (s, p, o), g, ix = rmat14
+    monkeypatch.setenv("GS_BATCH_POOL_BYTES", "4096")
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    pats = [q.patterns for q in rdfgen.queries(w, sm)]
+    b = g.eval_batch(pats)
+    for i, pt in enumerate(pats):
+        assert np.array_equal(b.fetch(i), ix.eval(pt, threads=4)), i
+    assert b.stats()[2] >= 1
+    b.close()
+
+
+def test_torch_allocator_hook(rmat14):
+    w, (s, p, o), _, ix = rmat14
+    alloc = gs.TorchAllocator()
+    g = gs.Graph(s, p, o, w.n_vertices, w.n_preds, allocator=alloc)
+    assert alloc.calls > 0
+    pats = [(-1, 2, -2), (-2, 3, -3)]
+    assert np.array_equal(g.query(pats), ix.eval(pats))
+    g.close()
+    assert not alloc.live        # everything handed back
+
+
+@pytest.mark.parametrize("fail_after", [1, 3, 6, 12])
+def test_allocation_failure_is_a_status(rmat14, fail_after):
+    # the hook refuses memory part-way through the store build: the call
+    # returns GS_ENOMEM, frees what it took, and the context stays usable
+    w, (s, p, o), g_ok, ix = rmat14
+    alloc = gs.TorchAllocator(fail_after=fail_after)
+    with pytest.raises(gs.GsError) as e:
+        gs.Graph(s, p, o, w.n_vertices, w.n_preds, allocator=alloc)
+    assert e.value.status == 2
+    assert not alloc.live
+    pats = [(-1, 2, -2)]
+    assert np.array_equal(g_ok.query(pats), ix.eval(pats))
+
+
+def test_server_answers_equal_alone(rmat14):
+    # continuous batching: the same queries submitted together, interleaved
+    # and repeated; every answer equals the query evaluated alone (and the
+    # oracle), and admitted memory never exceeds the budget
+    import time
+    w, (s, p, o), g, ix = rmat14
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    pats = [q.patterns for q in rdfgen.queries(w, sm)]
+    rng = np.random.default_rng(8)
+    for i in range(24):
+        sh = [rdfgen.star(2), rdfgen.chain(3), rdfgen.cycle(3), rdfgen.snowflake([1, 1])][i % 4]
+        sh.const = [int(rng.integers(0, sh.n_v))]
+        pats.append(sm.sample(sh, 123, i, 1e5).patterns)
+    alone = [g.query(pt) for pt in pats]
+    budget = 3 << 30
+    srv = gs.Server(g, max_batch=8, n_streams=3, memory_budget=budget)
+    plans = [g.plan(pt) for pt in pats]
+    order = list(range(len(pats))) * 2
+    rng.shuffle(order)
+    tickets = []
+    for j, qi in enumerate(order):
+        tickets.append((qi, srv.submit(plans[qi])))
+        if j % 5 == 0:
+            time.sleep(0.001)     # arrivals while earlier batches run
+    for qi, t in tickets:
+        t0 = time.time()
+        while not srv.poll(t)[0]:
+            assert time.time() - t0 < 60
+            time.sleep(0.0005)
+        got = srv.fetch(t)
+        assert np.array_equal(got, alone[qi]), qi
+        assert np.array_equal(got, ix.eval(pats[qi], threads=4)), qi
+        srv.release(t)
+    done, batches, peak = srv.stats()
+    assert done == len(order) and batches >= 2
+    assert peak <= budget
+    srv.stop()
