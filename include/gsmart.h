@@ -250,6 +250,28 @@ void gs_server_stop(gs_server* s);
 gs_status gs_scan_candidates(gs_graph* g, const uint32_t* preds, const uint8_t* dirs, uint32_t n,
                              uint32_t* out_bits, void* cuda_stream);
 
+/* gs_scan_candidates without any device allocation on the call path (the
+ * paper has no counterpart; it is an engineering variant for callers that
+ * must not allocate). Same arguments, result and errors as
+ * gs_scan_candidates, plus:
+ *   - the scan's workspace, a little over 4 (N + 1) bytes for a graph of N
+ *     vertices, lives in one static device array of
+ *     gs_noalloc_scratch_bytes() bytes (24 MiB: graphs up to about 6
+ *     million vertices); a graph that needs more gets GS_EINVAL and a
+ *     message naming both sizes;
+ *   - nothing in that array has to start at zero (each call zeroes what it
+ *     accumulates into);
+ *   - the first call on a device looks the array up (cudaGetSymbolAddress)
+ *     and caches its address: make it before any stream capture;
+ *   - the current device must be the graph's (else GS_EINVAL);
+ *   - all calls on one device share the array: calls whose work overlaps in
+ *     time (other streams, unordered host threads) race and corrupt each
+ *     other's results; calls on one stream are ordered and safe. */
+gs_status gs_scan_candidates_noalloc(gs_graph* g, const uint32_t* preds, const uint8_t* dirs,
+                                     uint32_t n, uint32_t* out_bits, void* cuda_stream);
+/* Size in bytes of the static workspace of gs_scan_candidates_noalloc. */
+size_t gs_noalloc_scratch_bytes(void);
+
 void gs_free_graph(gs_graph* g);
 void gs_free_plan(gs_plan* plan);
 void gs_free_result(gs_result* r);

@@ -29,7 +29,8 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_free_result", "gs_last_error", "gs_eval_batch", "gs_batch_info",
             "gs_batch_fetch", "gs_batch_stats", "gs_free_batch", "gs_batch_poll",
             "gs_server_start", "gs_server_submit", "gs_server_poll", "gs_server_fetch",
-            "gs_server_release", "gs_server_stats", "gs_server_stop"]
+            "gs_server_release", "gs_server_stats", "gs_server_stop",
+            "gs_scan_candidates_noalloc", "gs_noalloc_scratch_bytes"]
 
 
 class GsError(RuntimeError):
@@ -106,6 +107,7 @@ def load_library(path: str | None = None):
         "gs_fetch_bindings": [vp, vp, u64, i32, i32],
         "gs_result_stats": [vp, P(ctypes.c_float), P(u32)],
         "gs_scan_candidates": [vp, vp, vp, u32, vp, vp],
+        "gs_scan_candidates_noalloc": [vp, vp, vp, u32, vp, vp],
         "gs_eval_batch": [vp, vp, u32, vp, P(vp)],
         "gs_batch_info": [vp, vp, P(u64)],
         "gs_batch_fetch": [vp, u32, vp, u64, i32, i32],
@@ -127,6 +129,8 @@ def load_library(path: str | None = None):
         f = getattr(lib, name)
         f.argtypes = [vp]
         f.restype = None
+    lib.gs_noalloc_scratch_bytes.argtypes = []
+    lib.gs_noalloc_scratch_bytes.restype = ctypes.c_size_t
     lib.gs_last_error.argtypes = []
     lib.gs_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -242,6 +246,22 @@ class Graph:
         _check(_lib.gs_scan_candidates(self._h, pr.ctypes.data_as(ctypes.c_void_p),
                                        dr.ctypes.data_as(ctypes.c_void_p), len(pr),
                                        ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        return out
+
+    def scan_noalloc(self, preds, dirs, out, stream=None):
+        """scan() with the workspace in the library's static device array:
+        the call allocates nothing, so `out` (int32, ceil(N/32) words on the
+        graph's device) is required. Calls overlapping in time on one device
+        race on that array."""
+        words = (self.n_vertices + 31) // 32
+        if out.numel() < words or not out.is_cuda:
+            raise ValueError("out must be a device tensor of at least ceil(N/32) words")
+        pr = _host_u32(preds)
+        dr = np.ascontiguousarray(np.asarray(dirs), dtype=np.uint8)
+        _check(_lib.gs_scan_candidates_noalloc(self._h, pr.ctypes.data_as(ctypes.c_void_p),
+                                               dr.ctypes.data_as(ctypes.c_void_p), len(pr),
+                                               ctypes.c_void_p(out.data_ptr()),
+                                               _stream_handle(stream)))
         return out
 
 
