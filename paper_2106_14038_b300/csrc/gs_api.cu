@@ -119,6 +119,10 @@ gs_status wait_result(gs_result* r) {
             set_error("gs_eval_query: the answer has more than 2^40 rows under one binding");
             return GS_ENOMEM;
         }
+        if (head.status & kStStall) {
+            set_error("gs_eval_query: a bulk copy of the triple scan did not complete");
+            return GS_ETIMEOUT;
+        }
         if (head.status & kStEscalate) {
             // the single-block kernel handed the query back: run the grid path
             r->mode = 0;

@@ -317,7 +317,7 @@ gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, vo
     k_init<<<1, kThreads, 0, st>>>(E, cc);
     uint32_t nl_launch = 1;
     if (P->needs_scan) {
-        gs_status rc = run_scan(g, P->scan, E.bits, scan_work, st);
+        gs_status rc = run_scan(g, P->scan, E.bits, scan_work, st, &E.ctl->status);
         if (rc != GS_OK) return rc;
         nl_launch += 4;
     }

@@ -22,16 +22,18 @@ constexpr int kMaxSlots = 16;                // distinct predicates per directio
 constexpr int kBlocks = 1024;                // upper bound of the fixed grid (blocks)
 constexpr int kThreads = 256;
 
-// Rows whose degree exceeds kHeavyDeg are scanned in chunks of kHeavyChunk
-// entries, one warp per chunk, instead of inside their group of 32 rows.
-constexpr uint32_t kHeavyDeg = 8192;
-constexpr uint32_t kHeavyChunk = 16384;
-constexpr uint32_t kTileRows = 4096;      // rows per scan tile
-constexpr uint32_t kTileLabels = 8192;    // light labels per scan tile (+ one row)
+// Triple-scan work items. Each orientation is cut into items of equal cost
+// along the merge of its row ends and its labels (merge path): an item
+// holds at most kScanItemCost units, one per label and one per row end,
+// so it fits one shared-memory buffer and one pass of a warp whose 32 lanes
+// take kScanLabPer labels each.
+constexpr uint32_t kScanLabPer = 33;                       // labels per lane (odd: no bank conflicts)
+constexpr uint32_t kScanItemCost = 32 * kScanLabPer - 2;
 
 // Status bits written by kernels into the control block.
 constexpr uint32_t kStOverflow = 1u;  // a level or the output did not fit the workspace
 constexpr uint32_t kStBadInput = 2u;
+constexpr uint32_t kStStall = 16u;    // a bulk copy of the triple scan did not complete in time
 
 const char* last_error();
 
@@ -54,21 +56,19 @@ struct Alloc {
 
 // One orientation of the RDF matrix. Row r holds entries [ptr[r], ptr[r+1])
 // of idx (the other end) and lab (the predicate), sorted by (lab, idx).
-// idx and lab are padded with 4 zero words so aligned 16-byte loads that
-// start inside the array stay inside the allocation.
+// ptr, idx and lab are padded with 4 zero words so aligned 16-byte loads
+// and bulk copies that start inside the array stay inside the allocation.
 struct Store {
     uint32_t* ptr = nullptr;
     uint32_t* idx = nullptr;
     uint32_t* lab = nullptr;
-    // rows with more than kHeavyDeg entries, ascending, and their chunks
-    uint32_t* hrow = nullptr;       // [n_heavy]
-    uint32_t* chunk_h = nullptr;    // [n_chunks] index into hrow
-    uint32_t* chunk_start = nullptr;// [n_chunks] first entry of the chunk
-    uint32_t n_heavy = 0, n_chunks = 0;
-    // scan tiles (x = first row, y = row count): runs of light rows, at most
-    // kTileRows rows and kTileLabels + kHeavyDeg labels; never a heavy row
-    uint2* tiles = nullptr;
-    uint32_t n_tiles = 0;
+    // scan items: items[c] = (rows completed, labels consumed) before item c,
+    // c = 0..n_items (items[n_items] = (N, M))
+    uint2* items = nullptr;
+    uint32_t n_items = 0;
+    // bit k of heads: entry k is the first entry of its row
+    // (M / 32 + 8 words, zero past the last entry)
+    uint32_t* heads = nullptr;
 };
 
 // Device view passed to kernels by value.
@@ -184,9 +184,11 @@ gs_status radix_sort_u64(const gs_graph* g, uint64_t** keys, uint64_t** tmp, uin
 
 // scan.cu: candidate vectors (Eq. 17 / Eq. 21) of the variables in spec.
 // bits: spec.n_bvars vectors of ceil(N/32) words. work: scan_work_bytes().
+// status: a device word that receives kStStall if a bulk copy never
+// completes (NULL: a word inside work).
 size_t scan_work_bytes(const gs_graph* g);
 gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void* work,
-                   cudaStream_t st);
+                   cudaStream_t st, uint32_t* status = nullptr);
 
 // plan.cpp
 gs_status make_plan(const gs_graph* g, const int64_t* patterns, uint32_t n, uint32_t flags,

@@ -5,7 +5,7 @@
 // allocate device memory on the call path.
 //
 // Scratch: kNoAllocScratchBytes in the file-scope array below. The call
-// needs scan_work_bytes(g) of it (a little over 4 (N + 1) bytes) and
+// needs scan_work_bytes(g) of it (a little over 8 (N + 8) bytes) and
 // rejects graphs that need more. Nothing in the array has to start at
 // zero: the first kernel of every call zeroes every slot the scan ORs into
 // and its work counters; all other masks are written before they are read.
@@ -24,7 +24,7 @@
 
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = size_t(24) << 20;   // 24 MiB
+constexpr size_t kNoAllocScratchBytes = size_t(48) << 20;   // 48 MiB
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];

@@ -7,22 +7,36 @@
 // (Eq. 17 with only outgoing edges, Eq. 21 with both; Eq. 4 and Eq. 5 for
 // the single selections). All predicates of the query are tested in one
 // pass over the label array of each orientation:
-//   1. k_scan<false> streams the CSR labels and writes, per vertex, the mask
-//      of query out-predicates its row holds;
-//   2. k_scan<true> streams the CSC labels, forms the in-mask per vertex,
-//      combines it with the out-mask and ORs one bit per variable into the
-//      candidate vectors (warp ballot -> one word per 32 vertices);
-//   3. k_scan_fixup finishes the vertices whose column is heavy.
+//   1. k_scan streams the CSR labels and the CSC labels (one grid, items of
+//      both) and writes, per vertex, the mask of the query's out-predicates
+//      its row holds (mask_out) and of its in-predicates its column holds
+//      (mask_in);
+//   2. k_scan_eval combines the two masks per vertex and writes one bit per
+//      variable into the candidate vectors (warp ballot -> one word per 32
+//      vertices, so the vectors need no clearing).
+// k_scan_zero first clears the mask slots that several items OR into; each
+// kernel is launched to overlap the tail of the one before it
+// (programmatic dependent launch) and waits for it where it must.
 //
-// Work items, taken by CTAs from a device counter: store tiles (a run of at
-// most kTileRows light rows, whose labels are one contiguous span) and
-// chunks of kHeavyChunk entries of the rows longer than kHeavyDeg. A tile's
-// row pointers are loaded once into shared memory; its label span is then
-// staged in rounds of 8192 labels (coalesced 16-byte loads, a 16-bit one-hot
-// predicate bit per label in shared memory) and reduced per row by threads
-// that each OR 32 consecutive labels word by word (a segmented OR). Bytes moved per
-// pass: 4(N+1) row pointers + 4M labels, plus a 4N mask written and read
-// once and N/8 per vector.
+// Work decomposition. Each orientation is cut at store build into items of
+// equal cost along the merge of row ends and labels (merge path), so rows
+// of any degree and runs of empty rows cost the same per unit. A warp
+// takes items round robin and double-buffers them in shared memory: lanes
+// 0..2 move an item's labels, row-start bits and row pointers into its
+// buffer with bulk asynchronous copies that complete on an mbarrier, while
+// the warp works on the previous item. Warps never wait on one another.
+// Per item (row starts come from a bitmap built with the store):
+//   A. label phase: lane l takes 33 consecutive labels (an odd stride, so
+//      the 32 lanes hit 32 banks), maps each to its one-hot slot bit
+//      through a table and stores, per position, the OR since the later of
+//      its row's start and its lane's start; a segmented OR-scan over the
+//      lanes then gives, per lane, the OR of the row running through the
+//      lane's end;
+//   B. rows phase: one lane per row combines its last position's value with
+//      the previous lane's running total and writes the row's mask; a row
+//      that crosses an item boundary is ORed into its (zeroed) slot instead.
+// Bytes moved: per orientation 4(N+1) row pointers + 4M labels + M/8
+// row-start bits, a 4N mask written and read once, and N/8 per vector.
 #include <algorithm>
 
 #include "gs_device.cuh"
@@ -38,183 +52,120 @@ struct ScanDev {
     uint32_t n_out, n_in;
 };
 
-constexpr int kScanWarps = kThreads / 32;
-constexpr uint32_t kSpWords = (kTileRows + 1 + 3) & ~3u;   // row pointers, 16-byte padded
-constexpr int kScanUnroll = 4;   // 16-byte words per thread in flight
+constexpr uint32_t kItemLabs = 32 * kScanLabPer;         // label slots of one item (1056)
+constexpr uint32_t kGap = 36;                            // zeroed words after the labels
+constexpr uint32_t kHeadCopy = 48;                       // room for an item's row-start words
+constexpr uint32_t kBufWords = kItemLabs + 32 + kGap + kHeadCopy;   // labels | gap | starts | ptr | masks
+constexpr uint32_t kNumBuf = 2;                          // items in shared memory per warp
+constexpr uint32_t kScanWarps = 20;                      // most warps per CTA, each on its own items
+constexpr uint32_t kPmWords = kItemLabs / 2 + 32;        // 16-bit run ORs | 32 lane totals
+constexpr uint32_t kWarpWords = kNumBuf * kBufWords + kPmWords;
+constexpr long long kStallCycles = 4000000000LL;         // about 2 s at 2 GHz
+static_assert(kBufWords % 4 == 0 && kPmWords % 4 == 0 && kWarpWords % 4 == 0,
+              "bulk-copy destinations must stay 16-byte aligned");
 
-// label -> slot bit lookup in shared memory (P + 1 bytes: slot + 1, 0 = none)
-__device__ __forceinline__ void fill_lut(uint8_t* lut, uint32_t P, const uint32_t* preds,
-                                         uint32_t n) {
-    for (uint32_t i = threadIdx.x; i <= P + 1; i += blockDim.x) lut[i] = 0;
-    __syncthreads();
-    if (threadIdx.x < n) lut[preds[threadIdx.x]] = (uint8_t)(threadIdx.x + 1);
-    __syncthreads();
+// ---- bulk copies and mbarriers (inline PTX) ----
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ uint32_t lut_bit(const uint8_t* lut, uint32_t P, uint32_t l) {
-    uint32_t s = l <= P ? lut[l] : 0u;
-    return s ? (1u << (s - 1)) : 0u;
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
 }
 
-// Largest j in [lo, hi] with sp[j] <= pos (requires sp[lo] <= pos).
-__device__ __forceinline__ uint32_t search_row(const uint32_t* sp, uint32_t lo, uint32_t hi,
-                                               uint32_t pos) {
-    while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (sp[mid] <= pos) lo = mid; else hi = mid - 1;
-    }
-    return lo;
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// OR the query-predicate bits of one tile's labels into rm[0..nr).
-// sp[0..nr] are the tile's row pointers (all rows light; at most
-// kTileLabels + kHeavyDeg labels). The span is processed in rounds of
-// kRound labels: the CTA loads them with coalesced 16-byte loads and stores
-// each label's predicate bit (16-bit one-hot, 0 when not a query predicate)
-// in shared memory; then every thread ORs its kPerThread consecutive bits
-// word by word (two labels per 32-bit word) into the current row,
-// splitting a word only where a row boundary falls inside it, and ORs each
-// finished row into rm with one shared-memory atomic.
-constexpr uint32_t kPerThread = 32;
-constexpr uint32_t kRound = kThreads * kPerThread;        // 8192 labels per round
-
-// lut holds slot + 1 (0: not a query predicate); (1 << s) >> 1 is the one-hot bit.
-__device__ __forceinline__ uint32_t onehot(const uint8_t* lut, uint32_t P, uint32_t l) {
-    const uint32_t s = lut[min(l, P + 1)];
-    return (1u << s) >> 1;
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
 }
 
-__device__ __forceinline__ uint32_t fold16(uint32_t x) { return (x | (x >> 16)) & 0xffffu; }
-
-__device__ __forceinline__ void tile_masks(const uint32_t* __restrict__ lab, const uint32_t* sp,
-                                           uint32_t nr, uint32_t* rm, const uint8_t* lut,
-                                           uint32_t P, uint16_t* bits) {
-    const uint32_t ks = sp[0], ke = sp[nr];
-    const uint4* v = reinterpret_cast<const uint4*>(lab);
-    uint32_t rhint = 0;   // row of this thread's previous segment (rows only grow)
-    for (uint32_t c0 = ks & ~3u; c0 < ke; c0 += kRound) {
-        const uint32_t c1 = min(c0 + kRound, ke);
-        // stage: bits of positions [c0, c1) (0 outside [ks, c1)), zero up to the round's end
-        const uint32_t qa = c0 >> 2;
-        const uint32_t nw = (c1 - c0 + 3) >> 2;
-        constexpr uint32_t kBurst = 8;
-        for (uint32_t base = threadIdx.x; base < kRound / 4; base += kBurst * kThreads) {
-            uint4 x[kBurst];
-#pragma unroll
-            for (uint32_t u = 0; u < kBurst; ++u) {
-                const uint32_t wi = base + u * kThreads;
-                x[u] = wi < nw ? __ldcs(v + qa + wi) : make_uint4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (uint32_t u = 0; u < kBurst; ++u) {
-                const uint32_t wi = base + u * kThreads;
-                if (wi >= kRound / 4) break;
-                const uint32_t k = c0 + 4 * wi;
-                uint2 c = make_uint2(0, 0);
-                if (wi < nw) {
-                    uint32_t b0 = onehot(lut, P, x[u].x), b1 = onehot(lut, P, x[u].y);
-                    uint32_t b2 = onehot(lut, P, x[u].z), b3 = onehot(lut, P, x[u].w);
-                    if (k < ks || k + 3 >= c1) {           // an edge word of the span
-                        if (k < ks || k >= c1) b0 = 0;
-                        if (k + 1 < ks || k + 1 >= c1) b1 = 0;
-                        if (k + 2 < ks || k + 2 >= c1) b2 = 0;
-                        if (k + 3 < ks || k + 3 >= c1) b3 = 0;
-                    }
-                    c = make_uint2(b0 | (b1 << 16), b2 | (b3 << 16));
-                }
-                reinterpret_cast<uint2*>(bits)[wi] = c;
-            }
-        }
-        __syncthreads();
-        // consume: this thread's kPerThread consecutive positions, two per word
-        const uint32_t p0 = c0 + threadIdx.x * kPerThread;
-        const uint32_t first = max(p0, ks);
-        const uint32_t stop = min(p0 + kPerThread, c1);
-        if (first < stop) {
-            uint32_t r = search_row(sp, rhint, nr - 1, first);
-            uint32_t nxt = sp[r + 1];                 // start of the next row
-            uint32_t acc = 0;
-            const uint4* cw = reinterpret_cast<const uint4*>(bits + threadIdx.x * kPerThread);
-#pragma unroll
-            for (uint32_t i = 0; i < kPerThread / 8; ++i) {
-                const uint4 q = cw[i];
-                if (p0 + i * 8 + 8 <= nxt) {                   // all eight labels in row r
-                    acc |= q.x | q.y | q.z | q.w;
-                    continue;
-                }
-                const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                for (uint32_t t = 0; t < 4; ++t) {
-                    const uint32_t pos = p0 + i * 8 + t * 2;   // first of the word's two labels
-                    const uint32_t w = wv[t];
-                    if (pos + 2 <= nxt) {                      // both labels in row r
-                        acc |= w;
-                    } else if (w) {
-                        // a row boundary inside the word: place each half
-                        for (uint32_t h = 0; h < 2; ++h) {
-                            const uint32_t b = (w >> (16 * h)) & 0xffffu;
-                            if (!b) continue;
-                            const uint32_t pp = pos + h;
-                            if (pp >= nxt) {
-                                if (acc) atomicOr(rm + r, fold16(acc));
-                                acc = 0;
-                                while (sp[r + 1] <= pp) ++r;
-                                nxt = sp[r + 1];
-                            }
-                            acc |= b;
-                        }
-                    }
-                }
-            }
-            if (acc) atomicOr(rm + r, fold16(acc));
-            rhint = r;
-        }
-        __syncthreads();
-    }
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 
-// Block-cooperative OR over lab[b..e) (a heavy-row chunk).
-__device__ __forceinline__ uint32_t chunk_mask(const uint32_t* __restrict__ lab, uint32_t b,
-                                               uint32_t e, const uint8_t* lut, uint32_t P,
-                                               uint32_t* red) {
-    const uint4* v = reinterpret_cast<const uint4*>(lab);
-    const uint32_t q0 = b >> 2, q1 = (e + 3) >> 2;
-    constexpr uint32_t kStep = kThreads * kScanUnroll;
-    uint32_t m = 0;
-    for (uint32_t qb = q0; qb < q1; qb += kStep) {
-        uint4 x[kScanUnroll];
-#pragma unroll
-        for (int u = 0; u < kScanUnroll; ++u) {
-            uint32_t q = qb + (uint32_t)u * kThreads + threadIdx.x;
-            x[u] = q < q1 ? __ldcs(v + q) : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int u = 0; u < kScanUnroll; ++u) {
-            uint32_t k = (qb + (uint32_t)u * kThreads + threadIdx.x) << 2;
-            if (k >= b && k < e) m |= lut_bit(lut, P, x[u].x);
-            if (k + 1 >= b && k + 1 < e) m |= lut_bit(lut, P, x[u].y);
-            if (k + 2 >= b && k + 2 < e) m |= lut_bit(lut, P, x[u].z);
-            if (k + 3 >= b && k + 3 < e) m |= lut_bit(lut, P, x[u].w);
-        }
-    }
-    m = __reduce_or_sync(0xffffffffu, m);
-    if (lane_id() == 0) atomicOr(red, m);
-    __syncthreads();
-    return *red;
+// Wait for the phase with parity `parity` of bar, for at most kStallCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kStallCycles) return false;
+    return true;
 }
 
-// Heavy rows' mask slots, the candidate vectors and the work counters start
-// at zero; the chunks and tiles OR into them.
-__global__ void k_scan_zero(const uint32_t* __restrict__ hrow_out, uint32_t n_out_heavy,
-                            uint32_t* __restrict__ mask_out, uint32_t* __restrict__ hmask_in,
-                            uint32_t n_in_heavy, uint32_t* __restrict__ bits, uint64_t n_words,
-                            uint32_t* __restrict__ counters) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    for (uint32_t i = t; i < n_out_heavy; i += stride) mask_out[hrow_out[i]] = 0;
-    for (uint32_t i = t; i < n_in_heavy; i += stride) hmask_in[i] = 0;
-    for (uint64_t i = t; i < n_words; i += stride) bits[i] = 0;
-    if (t < 2) counters[t] = 0;
+// Global -> shared bulk copy; both addresses 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Item d = (r0, k0, r1, k1): rows r0..r1 (r1 only in part), labels
+// [k0, k1). Its buffer holds three regions, each copied from a 16-byte
+// boundary of global memory: labels from k0 & ~3 (nl words); after a gap
+// of at least 33 words that the warp zeroes, the row-start words covering
+// entries k0 .. k1 + 64 (nh words); row pointers from r0 & ~3 through row
+// r1 + 1 (np words).
+struct ItemLayout {
+    uint32_t nl, nh, np;
+    uint32_t ho, po;   // word offsets of the row starts and the row pointers
+};
+
+__device__ __forceinline__ uint32_t head_word0(uint32_t k0) { return (k0 >> 5) & ~3u; }
+
+__device__ __forceinline__ ItemLayout item_layout(uint4 d) {
+    ItemLayout L;
+    L.nl = ((d.w + 3u) & ~3u) - (d.y & ~3u);
+    L.nh = ((((d.w + 64u) >> 5) + 1u + 3u) & ~3u) - head_word0(d.y);
+    L.np = ((d.z + 2u + 3u) & ~3u) - (d.x & ~3u);
+    L.ho = (L.nl + 33u + 3u) & ~3u;
+    L.po = L.ho + L.nh;
+    return L;
+}
+
+// Lanes 0..2 of a warp put item d into buf behind bar, one region each,
+// with one copy instruction; lane 0 first announces the bytes. Called by
+// the whole warp.
+__device__ __forceinline__ void issue_item(uint32_t lane, uint32_t* buf, uint64_t* bar, uint4 d,
+                                           const DStore& S, const uint32_t* heads) {
+    const ItemLayout L = item_layout(d);
+    if (lane == 0) mbar_expect_tx(bar, 4u * (L.nl + L.nh + L.np));
+    __syncwarp();
+    const uint32_t* src = lane == 0 ? S.lab + (d.y & ~3u)
+                        : lane == 1 ? heads + head_word0(d.y)
+                                    : S.ptr + (d.x & ~3u);
+    const uint32_t off = lane == 0 ? 0u : lane == 1 ? L.ho : L.po;
+    const uint32_t n = lane == 0 ? L.nl : lane == 1 ? L.nh : L.np;
+    if (lane < 3 && n) bulk_g2s(buf + off, src, 4u * n, bar);
+}
+
+// label -> one-hot slot bit of this direction's query predicates
+template <typename LutT>
+__device__ __forceinline__ uint32_t lut_bit(const LutT* lut, uint32_t l);
+template <>
+__device__ __forceinline__ uint32_t lut_bit<uint16_t>(const uint16_t* lut, uint32_t l) {
+    return lut[l];
+}
+template <>
+__device__ __forceinline__ uint32_t lut_bit<uint8_t>(const uint8_t* lut, uint32_t l) {
+    return (1u << lut[l]) >> 1;   // the byte table holds slot + 1 (0: none)
 }
 
 __device__ __forceinline__ uint32_t eval_bits(const ScanDev& sd, uint32_t mo, uint32_t mi,
@@ -222,96 +173,280 @@ __device__ __forceinline__ uint32_t eval_bits(const ScanDev& sd, uint32_t mo, ui
     return ((mo & sd.need_out[u]) == sd.need_out[u]) && ((mi & sd.need_in[u]) == sd.need_in[u]);
 }
 
-// Pass 1 (EVAL = false): out-masks of all rows into mask_out.
-// Pass 2 (EVAL = true): in-masks of the light columns, combined with
-// mask_out into the candidate vectors; heavy columns go to hmask_in.
-template <bool EVAL>
-__global__ void __launch_bounds__(kThreads) k_scan(DStore S, uint32_t P, const uint2* __restrict__ tiles,
-                                                   uint32_t n_tiles,
-                                                   const uint32_t* __restrict__ chunk_h,
-                                                   const uint32_t* __restrict__ chunk_start,
-                                                   const uint32_t* __restrict__ hrow,
-                                                   uint32_t n_chunks, ScanDev sd,
-                                                   uint32_t* __restrict__ mask_out,
-                                                   uint32_t* __restrict__ hmask_in,
-                                                   uint32_t* __restrict__ bits, uint32_t words,
-                                                   uint32_t* counter) {
-    // dynamic shared memory: bits[kRound] (u16) | sp[kTileRows + 1] | rm[kTileRows] | lut[P + 2]
-    extern __shared__ __align__(16) uint8_t dsm[];
-    uint16_t* codes = (uint16_t*)dsm;
-    uint32_t* sp = (uint32_t*)(dsm + 2 * kRound);
-    uint32_t* rm = sp + kSpWords;
-    uint8_t* lut = (uint8_t*)(rm + kTileRows);
-    __shared__ uint32_t item_sh, red;
-    if (EVAL) fill_lut(lut, P, sd.in_pred, sd.n_in);
-    else fill_lut(lut, P, sd.out_pred, sd.n_out);
-    const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
-    const uint32_t items = n_chunks + n_tiles;   // heavy chunks first
-    for (;;) {
-        if (threadIdx.x == 0) item_sh = atomicAdd(counter, 1u);
-        __syncthreads();
-        const uint32_t it = item_sh;
-        __syncthreads();
-        if (it >= items) break;
-        if (it < n_chunks) {
-            const uint32_t h = ld(chunk_h + it);
-            const uint32_t r = ld(hrow + h);
-            const uint32_t b = ld(chunk_start + it);
-            const uint32_t e = min(b + kHeavyChunk, ld(S.ptr + r + 1));
-            if (threadIdx.x == 0) red = 0;
-            __syncthreads();
-            const uint32_t m = chunk_mask(S.lab, b, e, lut, P, &red);
-            if (threadIdx.x == 0 && m) atomicOr(EVAL ? hmask_in + h : mask_out + r, m);
-            __syncthreads();
-            continue;
+// Dynamic shared memory: per warp kNumBuf buffers | pm | head words; then the lut.
+template <typename LutT>
+size_t scan_smem_bytes(uint32_t P, uint32_t warps) {
+    return 4ull * warps * kWarpWords + 2 * sizeof(LutT) * ((size_t)P + 2);
+}
+
+// Warps per CTA that fit beside two luts of P + 2 entries of lut_bytes each.
+static uint32_t scan_warps_fit(uint32_t P, size_t lut_bytes) {
+    const size_t avail = 227u * 1024u - 1536u;   // less the static shared memory
+    const size_t lut = 2 * lut_bytes * ((size_t)P + 2);
+    if (lut >= avail) return 0;
+    return (uint32_t)std::min<size_t>(kScanWarps, (avail - lut) / (4ull * kWarpWords));
+}
+
+// One orientation of the matrix as the scan sees it.
+struct ScanSide {
+    DStore S;
+    const uint32_t* heads;
+    const uint2* items;
+    uint32_t n_items;
+    uint32_t* mask;   // per vertex: the query predicates of this direction its row holds
+};
+
+// Both orientations in one grid: items 0 .. out.n_items - 1 are the CSR's,
+// the rest the CSC's. Every warp works alone on its own items (round robin
+// over all warps of the grid) with its own buffers; it syncs only with
+// itself. Launched dependent on k_scan_zero: the first copies are issued
+// before waiting for it, the masks are written after.
+template <typename LutT>
+__global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanSide in, uint32_t N,
+                                                             uint32_t P, ScanDev sd,
+                                                             uint32_t* status) {
+    extern __shared__ __align__(128) uint32_t dsm[];
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint32_t n_warps = blockDim.x >> 5;
+    uint32_t* bufs = dsm + warp * kWarpWords;
+    uint16_t* pm = (uint16_t*)(bufs + kNumBuf * kBufWords);   // pm[p]: run OR at position p
+    uint32_t* cont = bufs + kNumBuf * kBufWords + kItemLabs / 2;   // cont[l]: lane l's run total
+    LutT* luts = (LutT*)(dsm + n_warps * kWarpWords);   // out-predicates | in-predicates
+    __shared__ __align__(8) uint64_t full[kScanWarps][kNumBuf];
+    __shared__ uint4 desc[kScanWarps][kNumBuf];
+    __shared__ uint32_t side_of[kScanWarps][kNumBuf];
+    const uint32_t n0 = out.n_items, n_items = out.n_items + in.n_items;
+
+    for (uint32_t i = threadIdx.x; i < 2 * (P + 2); i += blockDim.x) luts[i] = 0;
+    if (lane == 0) {
+        for (uint32_t b = 0; b < kNumBuf; ++b) mbar_init(&full[warp][b], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x < sd.n_out)
+        luts[sd.out_pred[threadIdx.x]] =
+            sizeof(LutT) == 2 ? (LutT)(1u << threadIdx.x) : (LutT)(threadIdx.x + 1);
+    if (threadIdx.x < sd.n_in)
+        luts[P + 2 + sd.in_pred[threadIdx.x]] =
+            sizeof(LutT) == 2 ? (LutT)(1u << threadIdx.x) : (LutT)(threadIdx.x + 1);
+    __syncthreads();
+
+    const uint32_t gw = blockIdx.x * n_warps + warp;
+    const uint32_t GW = gridDim.x * n_warps;
+    for (uint32_t b = 0; b < kNumBuf; ++b) {
+        const uint32_t c = gw + b * GW;
+        if (c < n_items) {
+            const bool cols = c >= n0;
+            const ScanSide& sd_ = cols ? in : out;
+            const uint32_t cl = cols ? c - n0 : c;
+            const uint2 a = sd_.items[cl], z = sd_.items[cl + 1];
+            const uint4 d = make_uint4(a.x, a.y, z.x, z.y);
+            if (lane == 0) { desc[warp][b] = d; side_of[warp][b] = cols; }
+            issue_item(lane, bufs + b * kBufWords, &full[warp][b], d, sd_.S, sd_.heads);
         }
-        const uint2 tl = tiles[it - n_chunks];
-        const uint32_t r0 = tl.x, nr = tl.y;
-        for (uint32_t j = threadIdx.x; j <= nr; j += kThreads) sp[j] = ld(S.ptr + r0 + j);
-        for (uint32_t j = threadIdx.x; j < nr; j += kThreads) rm[j] = 0;
-        __syncthreads();
-        tile_masks(S.lab, sp, nr, rm, lut, P, codes);
-        __syncthreads();
-        if (!EVAL) {
-            for (uint32_t j = threadIdx.x; j < nr; j += kThreads) mask_out[r0 + j] = rm[j];
-        } else {
-            // one warp per 32-vertex word overlapping the tile
-            const uint32_t w0 = r0 >> 5, w1 = (r0 + nr - 1) >> 5;
-            for (uint32_t wd = w0 + w; wd <= w1; wd += kScanWarps) {
-                const uint32_t v = wd * 32 + lane;
-                const bool in = v >= r0 && v < r0 + nr;
-                const uint32_t mi = in ? rm[v - r0] : 0u;
-                const uint32_t mo = in ? mask_out[v] : 0u;
-                for (uint32_t u = 0; u < sd.n_bvars; ++u) {
-                    uint32_t b = __ballot_sync(0xffffffffu, in && eval_bits(sd, mo, mi, u));
-                    if (lane == 0 && b) atomicOr(bits + (uint64_t)u * words + wd, b);
-                }
+    }
+    __syncwarp();
+    // the slots zeroed by k_scan_zero are written below
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    bool stalled = false;
+    uint32_t stall_i = 0;
+    for (uint32_t i = 0;; ++i) {
+        const uint32_t c = gw + i * GW;
+        if (c >= n_items) break;
+        const uint32_t b = i % kNumBuf;
+        const uint32_t cn = c + kNumBuf * GW;   // the item this buffer takes next
+        const bool ncols = cn >= n0;
+        uint2 nx = make_uint2(0, 0);   // lane 0: items[cn], lane 1: items[cn + 1] of its side
+        if (lane < 2 && cn < n_items)
+            nx = (ncols ? in.items : out.items)[(ncols ? cn - n0 : cn) + lane];   // in flight meanwhile
+        // every lane acquires the copies itself; all lanes agree on a stall
+        const bool landed = mbar_wait_bounded(&full[warp][b], (i / kNumBuf) & 1u);
+        if (!__all_sync(0xffffffffu, landed)) { stalled = true; stall_i = i; break; }
+
+        const uint4 d = desc[warp][b];
+        const uint32_t cols = side_of[warp][b];
+        const LutT* lut = luts + (cols ? P + 2 : 0u);
+        uint32_t* mask = cols ? in.mask : out.mask;
+        const uint32_t r0 = d.x, k0 = d.y, r1 = d.z, k1 = d.w;
+        const ItemLayout L = item_layout(d);
+        const uint32_t* buf = bufs + b * kBufWords;
+        uint32_t* lab = bufs + b * kBufWords + (k0 & 3u);       // lab[p]: label k0 + p
+        const uint32_t* hs = buf + L.ho;                       // row-start words from head_word0(k0)
+        const uint32_t* pp = buf + L.po + (r0 & 3u);           // pp[j]: ptr[r0 + j]
+        const uint32_t nk = k1 - k0;
+        const uint32_t nt = r1 - r0 + (r1 < N ? 1u : 0u);     // rows touched
+        // label 0 (no predicate) in the 33 positions after the item's labels
+        lab[nk + lane] = 0;
+        if (lane == 0) lab[nk + 32] = 0;
+
+        // A. label phase: pm[p] = OR of the one-hot bits from the later of
+        // (the head of p's row, the start of p's lane) through p
+        const uint32_t base = lane * kScanLabPer;
+        uint32_t acc = 0;
+        bool has_head = false;
+        if (base < nk) {   // positions past nk read label 0
+            // row starts of entries k0 + base .. + 32; a start past k1 only
+            // touches positions no row reads back
+            const uint32_t gp = k0 + base;
+            const uint32_t hwi = (gp >> 5) - head_word0(k0);
+            const uint64_t h64 = ((((uint64_t)hs[hwi + 1]) << 32) | hs[hwi]) >> (gp & 31);
+            // all loads first: the stores into pm below may not be
+            // reordered before loads of the same shared array
+            uint32_t v[kScanLabPer];
+#pragma unroll
+            for (uint32_t q = 0; q < kScanLabPer; ++q) v[q] = lab[base + q];
+#pragma unroll
+            for (uint32_t q = 0; q < kScanLabPer; ++q) v[q] = lut_bit<LutT>(lut, v[q]);
+#pragma unroll
+            for (uint32_t q = 0; q < kScanLabPer; ++q) {
+                const uint32_t keep = (uint32_t)((h64 >> q) & 1ull) - 1u;   // 0 at a head
+                acc = (acc & keep) | v[q];
+                pm[base + q] = (uint16_t)acc;
             }
+            has_head = (h64 & ((1ull << kScanLabPer) - 1)) != 0;
         }
-        __syncthreads();
+        // segmented inclusive OR-scan of the lanes' last runs; a lane holding
+        // a head starts a segment: cont[l] = OR of the labels from the
+        // head of the row at the end of lane l through that end
+        {
+            bool f = has_head;
+#pragma unroll
+            for (uint32_t o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, acc, o);
+                const bool g = __shfl_up_sync(0xffffffffu, f, o);
+                if (lane >= o && !f) acc |= v;
+                if (lane >= o) f = f || g;
+            }
+            cont[lane] = acc;
+        }
+        __syncwarp();
+
+        // B. rows phase: a row's labels [lo, hi) in the item end in lane lb;
+        // the part in lane lb is pm[hi - 1 - k0], the part before it the run
+        // total of lane lb - 1
+        for (uint32_t j = lane; j < nt; j += 32) {
+            const uint32_t r = r0 + j;
+            const uint32_t s = pp[j], e = pp[j + 1];
+            const uint32_t lo = max(s, k0), hi = min(e, k1);
+            uint32_t m = 0;
+            if (lo < hi) {
+                const uint32_t la = (lo - k0) / kScanLabPer, lb = (hi - 1 - k0) / kScanLabPer;
+                m = pm[hi - 1 - k0] | (lb > la ? cont[lb - 1] : 0u);
+            }
+            if (r < r1 && s >= k0) mask[r] = m;     // the row lies in this item
+            else if (m) atomicOr(mask + r, m);       // it crosses an item boundary
+        }
+        __syncwarp();   // buffer b and pm are free again
+        if (cn < n_items) {
+            const uint4 d2 = make_uint4(__shfl_sync(0xffffffffu, nx.x, 0), __shfl_sync(0xffffffffu, nx.y, 0),
+                                        __shfl_sync(0xffffffffu, nx.x, 1), __shfl_sync(0xffffffffu, nx.y, 1));
+            if (lane == 0) { desc[warp][b] = d2; side_of[warp][b] = ncols; }
+            // the gap was zeroed through the generic proxy; the copies into
+            // this buffer go through the async proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const ScanSide& ns = ncols ? in : out;
+            issue_item(lane, bufs + b * kBufWords, &full[warp][b], d2, ns.S, ns.heads);
+        }
+        __syncwarp();
+    }
+
+    // the candidate-bit kernel may start launching (it waits for this grid)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (stalled && lane == 0) {
+        // report, then let the copies still in flight (items stall_i ..
+        // stall_i + kNumBuf - 1 of this warp) land before the warp exits
+        atomicOr(status, kStStall);
+        for (uint32_t k = stall_i; k < stall_i + kNumBuf; ++k)
+            if (gw + k * GW < n_items) mbar_wait_bounded(&full[warp][k % kNumBuf], (k / kNumBuf) & 1u);
     }
 }
 
-// Pass 3: vertices with a heavy column.
-__global__ void k_scan_fixup(const uint32_t* __restrict__ hrow_in, uint32_t n_in_heavy,
-                             ScanDev sd, const uint32_t* __restrict__ mask_out,
-                             const uint32_t* __restrict__ hmask_in, uint32_t* __restrict__ bits,
-                             uint32_t words) {
-    for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n_in_heavy;
-         h += gridDim.x * blockDim.x) {
-        uint32_t v = hrow_in[h];
-        uint32_t mo = mask_out[v], mi = hmask_in[h];
-        for (uint32_t u = 0; u < sd.n_bvars; ++u)
-            if (eval_bits(sd, mo, mi, u)) atomicOr(bits + (uint64_t)u * words + (v >> 5), 1u << (v & 31));
+// The mask slots of rows that cross item boundaries start at zero: the
+// items OR their parts into them.
+__global__ void k_scan_zero(const uint32_t* __restrict__ ptr_out, const uint2* __restrict__ items_out,
+                            uint32_t n_out, const uint32_t* __restrict__ ptr_in,
+                            const uint2* __restrict__ items_in, uint32_t n_in,
+                            uint32_t* __restrict__ mask_out, uint32_t* __restrict__ mask_in,
+                            uint32_t* __restrict__ status) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // k_scan may start its copies
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint32_t c = 1 + t; c < n_out; c += stride) {
+        const uint2 it = items_out[c];
+        if (ptr_out[it.x] < it.y) mask_out[it.x] = 0;
+    }
+    for (uint32_t c = 1 + t; c < n_in; c += stride) {
+        const uint2 it = items_in[c];
+        if (ptr_in[it.x] < it.y) mask_in[it.x] = 0;
+    }
+    if (t == 0 && status) *status = 0;
+}
+
+// Candidate bits: vertex v is a candidate of variable u when its row holds
+// every out-predicate and its column every in-predicate u needs (Eq. 21).
+// One thread per vertex; each warp writes the whole word of its 32.
+__global__ void k_scan_eval(const uint32_t* __restrict__ mask_out,
+                            const uint32_t* __restrict__ mask_in, uint32_t N, ScanDev sd,
+                            uint32_t* __restrict__ bits, uint32_t words) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the masks of k_scan
+    const uint32_t lane = lane_id();
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v - lane < N;
+         v += gridDim.x * blockDim.x) {
+        const bool in = v < N;
+        const uint32_t mo = in ? __ldcs(mask_out + v) : 0u, mi = in ? __ldcs(mask_in + v) : 0u;
+        for (uint32_t u = 0; u < sd.n_bvars; ++u) {
+            const uint32_t b = __ballot_sync(0xffffffffu, in && eval_bits(sd, mo, mi, u));
+            if (lane == 0) bits[(uint64_t)u * words + (v >> 5)] = b;
+        }
     }
 }
 
+// Workspace: mask_out (N + 8 words) | mask_in (N + 8 words) | status word.
 size_t scan_work_bytes(const gs_graph* g) {
-    return sizeof(uint32_t) * ((uint64_t)g->N + 1) + sizeof(uint32_t) * (g->in.n_heavy + 1) + 512;
+    return 8ull * ((uint64_t)g->N + 8) + 512;
+}
+
+// Launch with programmatic stream serialization: the kernel may start
+// while the previous one in the stream finishes; it waits for it with
+// griddepcontrol.wait before touching what that one writes.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <typename LutT>
+static gs_status launch_scan(const gs_graph* g, const ScanDev& sd, uint32_t* mask_out,
+                             uint32_t* mask_in, uint32_t* status, uint32_t warps, cudaStream_t st) {
+    const size_t smem = scan_smem_bytes<LutT>(g->P, warps);
+    static size_t smem_set = 0;
+    if (smem > smem_set) {
+        GS_CUDA(cudaFuncSetAttribute(k_scan<LutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        smem_set = smem;
+    }
+    // one CTA per SM (the shared memory admits no second one)
+    const uint32_t n_items = g->out.n_items + g->in.n_items;
+    const uint32_t grid = std::max(1u, std::min((uint32_t)g->sm_count, (n_items + warps - 1) / warps));
+    const ScanSide out{dview(g->out), g->out.heads, g->out.items, g->out.n_items, mask_out};
+    const ScanSide in{dview(g->in), g->in.heads, g->in.items, g->in.n_items, mask_in};
+    GS_CUDA(launch_dependent(k_scan<LutT>, dim3(grid), dim3(warps * 32), smem, st, out, in, g->N,
+                             g->P, sd, status));
+    return GS_OK;
 }
 
 gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void* work,
-                   cudaStream_t st) {
+                   cudaStream_t st, uint32_t* status) {
     ScanDev sd{};
     sd.n_bvars = spec.n_bvars;
     sd.n_out = spec.n_out;
@@ -323,39 +458,27 @@ gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void
         sd.need_in[u] = spec.need_in[u];
     }
     uint32_t* mask_out = (uint32_t*)work;
-    uint32_t* hmask_in = mask_out + ((uint64_t)g->N + 1);
-    uint32_t* counters = hmask_in + (g->in.n_heavy + 1);    // two work counters
+    uint32_t* mask_in = mask_out + ((uint64_t)g->N + 8);
+    const bool own = status == nullptr;
+    if (own) status = mask_in + ((uint64_t)g->N + 8);
     const uint32_t words = (g->N + 31) / 32;
-    const size_t smem = 2 * (size_t)kRound + 4 * (size_t)kSpWords + 4 * (size_t)kTileRows + g->P + 2;
-    static int per_sm = 0;
-    static size_t smem_set = 0;
-    if (smem > smem_set) {
-        GS_CUDA(cudaFuncSetAttribute(k_scan<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        GS_CUDA(cudaFuncSetAttribute(k_scan<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = smem;
-        per_sm = 0;
-    }
-    if (per_sm == 0) {
-        int a = 0, b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_scan<false>, kThreads, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan<true>, kThreads, smem);
-        per_sm = std::max(1, std::min(a, b));
-    }
     const int nb = g->n_blocks;
-    const int nbs = g->sm_count * per_sm;   // one wave of resident blocks
-    k_scan_zero<<<nb, kThreads, 0, st>>>(g->out.hrow, g->out.n_heavy, mask_out, hmask_in,
-                                         g->in.n_heavy, bits, (uint64_t)words * spec.n_bvars,
-                                         counters);
-    k_scan<false><<<nbs, kThreads, smem, st>>>(dview(g->out), g->P, g->out.tiles, g->out.n_tiles,
-                                              g->out.chunk_h, g->out.chunk_start, g->out.hrow,
-                                              g->out.n_chunks, sd, mask_out, hmask_in, bits,
-                                              words, counters);
-    k_scan<true><<<nbs, kThreads, smem, st>>>(dview(g->in), g->P, g->in.tiles, g->in.n_tiles,
-                                             g->in.chunk_h, g->in.chunk_start, g->in.hrow,
-                                             g->in.n_chunks, sd, mask_out, hmask_in, bits, words,
-                                             counters + 1);
-    k_scan_fixup<<<nb, kThreads, 0, st>>>(g->in.hrow, g->in.n_heavy, sd, mask_out, hmask_in, bits,
-                                          words);
+    k_scan_zero<<<nb, kThreads, 0, st>>>(g->out.ptr, g->out.items, g->out.n_items, g->in.ptr,
+                                         g->in.items, g->in.n_items, mask_out, mask_in,
+                                         own ? status : nullptr);
+    // the 16-bit one-hot table unless it costs more than a few warps
+    const uint32_t w16 = scan_warps_fit(g->P, sizeof(uint16_t));
+    const uint32_t w8 = scan_warps_fit(g->P, sizeof(uint8_t));
+    gs_status rc;
+    if (w16 >= 12 || w16 >= w8)
+        rc = launch_scan<uint16_t>(g, sd, mask_out, mask_in, status, w16, st);
+    else
+        rc = launch_scan<uint8_t>(g, sd, mask_out, mask_in, status, w8, st);
+    if (rc != GS_OK) return rc;
+    const uint32_t eb = (uint32_t)std::min<uint64_t>(((uint64_t)words * 32 + kThreads - 1) / kThreads, 1u << 20);
+    GS_CUDA(launch_dependent(k_scan_eval, dim3(std::max(1u, eb)), dim3(kThreads), 0, st,
+                             (const uint32_t*)mask_out, (const uint32_t*)mask_in, g->N, sd, bits,
+                             words));
     GS_CUDA(cudaGetLastError());
     return GS_OK;
 }

@@ -4,8 +4,8 @@
 //
 // Steps, all on the device: pack each triple into a 64-bit key
 // (row | label | col), LSD radix sort, drop equal neighbours, split the
-// keys into idx / lab arrays and derive the row pointers; then list the
-// rows longer than kHeavyDeg and cut them into chunks for the scan.
+// keys into idx / lab arrays and derive the row pointers; then cut the
+// orientation into the triple scan's equal-cost work items.
 #include <algorithm>
 #include <cstring>
 
@@ -210,82 +210,30 @@ __global__ void k_ptr_tail(const uint64_t* __restrict__ keys, uint64_t n, int vb
         ptr[r] = (uint32_t)M;
 }
 
-// Heavy rows: per row, (1 << 36) per heavy row plus its chunk count.
-constexpr int kHeavyShift = 36;
-
-__global__ void k_heavy_counts(const uint32_t* __restrict__ ptr, uint32_t N,
-                               uint64_t* __restrict__ cnt) {
-    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
-         r += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t d = ptr[r + 1] - ptr[r];
-        cnt[r] = d > kHeavyDeg ? ((1ull << kHeavyShift) | ((d + kHeavyChunk - 1) / kHeavyChunk)) : 0ull;
+// Row-start bits: bit ptr[r] for every non-empty row r.
+__global__ void k_heads(const uint32_t* __restrict__ ptr, uint32_t N, uint32_t* __restrict__ heads) {
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
+        const uint32_t b = ptr[r];
+        if (b < ptr[r + 1]) atomicOr(heads + (b >> 5), 1u << (b & 31));
     }
 }
 
-__global__ void k_heavy_write(const uint32_t* __restrict__ ptr, uint32_t N,
-                              const uint64_t* __restrict__ off, uint32_t* __restrict__ hrow,
-                              uint32_t* __restrict__ chunk_h, uint32_t* __restrict__ chunk_start) {
-    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
-         r += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t b = ptr[r], d = ptr[r + 1] - b;
-        if (d <= kHeavyDeg) continue;
-        uint64_t o = off[r];
-        uint32_t h = (uint32_t)(o >> kHeavyShift);
-        uint64_t c = o & ((1ull << kHeavyShift) - 1);
-        hrow[h] = (uint32_t)r;
-        uint32_t nc = (d + kHeavyChunk - 1) / kHeavyChunk;
-        for (uint32_t j = 0; j < nc; ++j) {
-            chunk_h[c + j] = h;
-            chunk_start[c + j] = b + j * kHeavyChunk;
+// Scan items (merge path over row ends and labels): boundary c sits at cost
+// d = min(c * kScanItemCost, w N + M); the rows completed before it are the
+// largest r with w r + ptr[r] <= d, the labels consumed min(d - w r, ptr[r+1]).
+__global__ void k_items(const uint32_t* __restrict__ ptr, uint32_t N, uint64_t M, uint32_t w,
+                        uint32_t n_items, uint2* __restrict__ items) {
+    const uint64_t total = (uint64_t)w * N + M;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c <= n_items;
+         c += gridDim.x * blockDim.x) {
+        const uint64_t d = min((uint64_t)c * kScanItemCost, total);
+        uint32_t lo = 0, hi = N;                      // w * 0 + ptr[0] = 0 <= d
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo + 1) / 2;
+            if ((uint64_t)w * mid + ptr[mid] <= d) lo = mid; else hi = mid - 1;
         }
-    }
-}
-
-// Scan tiles: runs of consecutive light rows (degree <= kHeavyDeg) cut
-// every kTileLabels light labels, every kTileRows rows and at every heavy
-// row. With pre[r] = (heavy rows before r) << 40 | (light labels before r),
-// a light row's tile key is (heavy rows before, light labels / kTileLabels,
-// r / kTileRows); a tile is a maximal run of light rows with one key, so it
-// holds at most kTileRows rows and kTileLabels + kHeavyDeg labels.
-constexpr uint64_t kLow40 = (1ull << 40) - 1;
-
-__device__ __forceinline__ uint64_t tile_key(uint64_t pre, uint32_t r) {
-    return ((pre >> 40) << 40) | ((uint64_t)(r / kTileRows) << 20) | ((pre & kLow40) / kTileLabels);
-}
-
-__global__ void k_tile_prep(const uint32_t* __restrict__ ptr, uint32_t N, uint64_t* __restrict__ val) {
-    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
-         r += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t d = ptr[r + 1] - ptr[r];
-        val[r] = d > kHeavyDeg ? (1ull << 40) : (uint64_t)d;
-    }
-}
-
-__device__ __forceinline__ bool tile_start(const uint32_t* __restrict__ ptr,
-                                           const uint64_t* __restrict__ pre, uint32_t r) {
-    if (ptr[r + 1] - ptr[r] > kHeavyDeg) return false;
-    if (r == 0) return true;
-    if (ptr[r] - ptr[r - 1] > kHeavyDeg) return true;
-    return tile_key(pre[r], r) != tile_key(pre[r - 1], r - 1);
-}
-
-__global__ void k_tile_flags(const uint32_t* __restrict__ ptr, uint32_t N,
-                             const uint64_t* __restrict__ pre, uint64_t* __restrict__ flg) {
-    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
-         r += (uint64_t)gridDim.x * blockDim.x)
-        flg[r] = tile_start(ptr, pre, (uint32_t)r) ? 1ull : 0ull;
-}
-
-__global__ void k_tile_write(const uint32_t* __restrict__ ptr, uint32_t N,
-                             const uint64_t* __restrict__ pre, const uint64_t* __restrict__ tix,
-                             uint2* __restrict__ tiles) {
-    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
-         r += (uint64_t)gridDim.x * blockDim.x) {
-        if (!tile_start(ptr, pre, (uint32_t)r)) continue;
-        const uint64_t key = tile_key(pre[r], (uint32_t)r);
-        uint32_t e = (uint32_t)r + 1;
-        while (e < N && ptr[e + 1] - ptr[e] <= kHeavyDeg && tile_key(pre[e], e) == key) ++e;
-        tiles[tix[r]] = make_uint2((uint32_t)r, e - (uint32_t)r);
+        const uint64_t k = lo < N ? min(d - (uint64_t)w * lo, (uint64_t)ptr[lo + 1]) : M;
+        items[c] = make_uint2(lo, (uint32_t)k);
     }
 }
 
@@ -325,85 +273,38 @@ static gs_status build_dir(gs_graph* g, const uint32_t* s, const uint32_t* p, co
         return GS_EINVAL;
     }
     g->M = M;
-    S.ptr = (uint32_t*)g->alloc.get(sizeof(uint32_t) * ((uint64_t)g->N + 1), st);
+    S.ptr = (uint32_t*)g->alloc.get(sizeof(uint32_t) * ((uint64_t)g->N + 1 + 4), st);
     S.idx = (uint32_t*)g->alloc.get(sizeof(uint32_t) * (M + 4), st);
     S.lab = (uint32_t*)g->alloc.get(sizeof(uint32_t) * (M + 4), st);
     if (!S.ptr || !S.idx || !S.lab) { set_error("gs_load_triples: out of device memory"); return GS_ENOMEM; }
+    GS_CUDA(cudaMemsetAsync(S.ptr + g->N + 1, 0, 16, st));
     GS_CUDA(cudaMemsetAsync(S.idx + M, 0, 16, st));
     GS_CUDA(cudaMemsetAsync(S.lab + M, 0, 16, st));
     k_uniq_write<<<nb, kThreads, 0, st>>>(keys, n_dev, boff, vb, lb, S.idx, S.lab, S.ptr);
     k_ptr_tail<<<nb, kThreads, 0, st>>>(keys, n, vb, lb, g->N, M, S.ptr);
     GS_CUDA(cudaGetLastError());
 
-    // heavy rows and their chunks
-    uint64_t* cnt = tmp;   // N + 1 entries fit: tmp holds n >= ... keys; use a fresh buffer if short
-    bool own_cnt = false;
-    if (n < (uint64_t)g->N + 1) {
-        cnt = (uint64_t*)g->alloc.get(sizeof(uint64_t) * ((uint64_t)g->N + 1), st);
-        if (!cnt) { set_error("gs_load_triples: out of device memory"); return GS_ENOMEM; }
-        own_cnt = true;
+    // scan items
+    const uint32_t w = 1;   // one cost unit per row end
+    const uint64_t cost = (uint64_t)w * g->N + M;
+    const uint64_t ni = (cost + kScanItemCost - 1) / kScanItemCost;
+    if (ni >= (1ull << 31)) {
+        set_error("gs_load_triples: %llu scan items exceed the 31-bit item index",
+                  (unsigned long long)ni);
+        return GS_EINVAL;
     }
-    uint64_t nrows = g->N;
-    GS_CUDA(cudaMemcpyAsync(n_dev, &nrows, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-    k_heavy_counts<<<nb, kThreads, 0, st>>>(S.ptr, g->N, cnt);
-    k_block_sums_u64<<<nb, kThreads, 0, st>>>(cnt, n_dev, bsum, nullptr);
-    k_scan_block_sums<<<1, kThreads, 0, st>>>(bsum, boff, nb, tot, nullptr);
-    k_scan_apply_u64<<<nb, kThreads, 0, st>>>(cnt, n_dev, boff, nullptr);
-    uint64_t ht = 0;
-    GS_CUDA(cudaMemcpyAsync(&ht, tot, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    GS_CUDA(cudaStreamSynchronize(st));
-    S.n_heavy = (uint32_t)(ht >> kHeavyShift);
-    S.n_chunks = (uint32_t)(ht & ((1ull << kHeavyShift) - 1));
-    S.hrow = (uint32_t*)g->alloc.get(sizeof(uint32_t) * (S.n_heavy + 1), st);
-    S.chunk_h = (uint32_t*)g->alloc.get(sizeof(uint32_t) * (S.n_chunks + 1), st);
-    S.chunk_start = (uint32_t*)g->alloc.get(sizeof(uint32_t) * (S.n_chunks + 1), st);
-    if (!S.hrow || !S.chunk_h || !S.chunk_start) {
-        if (own_cnt) g->alloc.put(cnt, st);
-        set_error("gs_load_triples: out of device memory");
-        return GS_ENOMEM;
-    }
-    k_heavy_write<<<nb, kThreads, 0, st>>>(S.ptr, g->N, cnt, S.hrow, S.chunk_h, S.chunk_start);
+    S.n_items = (uint32_t)ni;
+    S.items = (uint2*)g->alloc.get(sizeof(uint2) * (ni + 1), st);
+    if (!S.items) { set_error("gs_load_triples: out of device memory"); return GS_ENOMEM; }
+    k_items<<<(unsigned)std::min<uint64_t>((ni + kThreads) / kThreads, (uint64_t)nb), kThreads, 0, st>>>(
+        S.ptr, g->N, M, w, S.n_items, S.items);
+    const uint64_t hwords = M / 32 + 8;
+    S.heads = (uint32_t*)g->alloc.get(sizeof(uint32_t) * hwords, st);
+    if (!S.heads) { set_error("gs_load_triples: out of device memory"); return GS_ENOMEM; }
+    GS_CUDA(cudaMemsetAsync(S.heads, 0, sizeof(uint32_t) * hwords, st));
+    k_heads<<<nb, kThreads, 0, st>>>(S.ptr, g->N, S.heads);
     GS_CUDA(cudaGetLastError());
     GS_CUDA(cudaStreamSynchronize(st));
-
-    // scan tiles: pre = prefix of (heavy << 40 | light degree), flags, their prefix
-    uint64_t* flg = keys;   // the sorted keys are no longer needed
-    bool own_flg = false;
-    if (n < (uint64_t)g->N + 1) {
-        flg = (uint64_t*)g->alloc.get(sizeof(uint64_t) * ((uint64_t)g->N + 1), st);
-        if (!flg) {
-            if (own_cnt) g->alloc.put(cnt, st);
-            set_error("gs_load_triples: out of device memory");
-            return GS_ENOMEM;
-        }
-        own_flg = true;
-    }
-    k_tile_prep<<<nb, kThreads, 0, st>>>(S.ptr, g->N, cnt);
-    k_block_sums_u64<<<nb, kThreads, 0, st>>>(cnt, n_dev, bsum, nullptr);
-    k_scan_block_sums<<<1, kThreads, 0, st>>>(bsum, boff, nb, tot, nullptr);
-    k_scan_apply_u64<<<nb, kThreads, 0, st>>>(cnt, n_dev, boff, nullptr);
-    k_tile_flags<<<nb, kThreads, 0, st>>>(S.ptr, g->N, cnt, flg);
-    k_block_sums_u64<<<nb, kThreads, 0, st>>>(flg, n_dev, bsum, nullptr);
-    k_scan_block_sums<<<1, kThreads, 0, st>>>(bsum, boff, nb, tot, nullptr);
-    k_scan_apply_u64<<<nb, kThreads, 0, st>>>(flg, n_dev, boff, nullptr);
-    uint64_t nt = 0;
-    GS_CUDA(cudaMemcpyAsync(&nt, tot, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    GS_CUDA(cudaStreamSynchronize(st));
-    S.n_tiles = (uint32_t)nt;
-    S.tiles = (uint2*)g->alloc.get(sizeof(uint2) * (nt + 1), st);
-    if (!S.tiles) {
-        if (own_cnt) g->alloc.put(cnt, st);
-        if (own_flg) g->alloc.put(flg, st);
-        set_error("gs_load_triples: out of device memory");
-        return GS_ENOMEM;
-    }
-    k_tile_write<<<nb, kThreads, 0, st>>>(S.ptr, g->N, cnt, flg, S.tiles);
-    GS_CUDA(cudaGetLastError());
-    GS_CUDA(cudaStreamSynchronize(st));
-    if (own_flg) g->alloc.put(flg, st);
-    GS_CUDA(cudaGetLastError());
-    GS_CUDA(cudaStreamSynchronize(st));
-    if (own_cnt) g->alloc.put(cnt, st);
     return GS_OK;
 }
 
@@ -447,8 +348,8 @@ gs_status build_store(gs_graph* g, const uint32_t* s, const uint32_t* p, const u
 void free_store(gs_graph* g, cudaStream_t st) {
     for (Store* S : {&g->out, &g->in}) {
         g->alloc.put(S->ptr, st); g->alloc.put(S->idx, st); g->alloc.put(S->lab, st);
-        g->alloc.put(S->hrow, st); g->alloc.put(S->chunk_h, st); g->alloc.put(S->chunk_start, st);
-        g->alloc.put(S->tiles, st);
+        g->alloc.put(S->items, st);
+        g->alloc.put(S->heads, st);
         *S = Store{};
     }
 }

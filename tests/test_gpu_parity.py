@@ -136,6 +136,36 @@ def test_scan_heavy_rows_and_ragged_tail():
     assert _bits_to_bool(g.scan([3, 6], [0, 0]), n_v)[7]
 
 
+@pytest.mark.parametrize("shape", ["hubs", "sparse"])
+def test_scan_rows_crossing_work_items(shape):
+    # the scan cuts each orientation into work items of about 8.4K units
+    # (labels + row ends): "hubs" has a 60,000-entry row and a 50,000-entry
+    # column that cross many items, with the column on the last vertex;
+    # "sparse" is mostly empty rows, so items hold thousands of rows
+    rng = np.random.default_rng(17)
+    if shape == "hubs":
+        n_v, n_p = 70001, 5
+        s = np.concatenate([np.full(60000, 5), rng.integers(0, n_v, 50000), rng.integers(0, n_v, 20000)])
+        o = np.concatenate([rng.integers(0, n_v, 60000), np.full(50000, n_v - 1), rng.integers(0, n_v, 20000)])
+        p = np.concatenate([1 + np.arange(60000) % 4, rng.integers(1, n_p + 1, 50000),
+                            rng.integers(1, n_p + 1, 20000)])
+        p[60000 + 777] = 5                       # one rare label inside the hub column
+    else:
+        n_v, n_p = 300001, 4
+        s, o = rng.integers(0, n_v, 500), rng.integers(0, n_v, 500)
+        p = rng.integers(1, n_p + 1, 500)
+    g, ix = _graph(s, p, o, n_v, n_p)
+    cases = list(_scan_cases(n_p, rng, 25)) + [([1, 2, 3, 4], [0, 0, 0, 0])]
+    if shape == "hubs":
+        cases.append(([5], [1]))
+    for preds, dirs in cases:
+        want = np.ones(n_v, bool)
+        for q, d in zip(preds, dirs):
+            want &= ix.presence(int(d), int(q)).astype(bool)
+        got = _bits_to_bool(g.scan(preds, dirs), n_v)
+        assert np.array_equal(got, want), (shape, preds, dirs)
+
+
 def _same(g, ix, pats, flags=0):
     got = g.query(pats, sort=True, flags=flags)
     want = ix.eval(pats, threads=4)
