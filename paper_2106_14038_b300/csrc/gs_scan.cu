@@ -385,26 +385,39 @@ __global__ void k_scan_zero(const uint32_t* __restrict__ ptr_out, const uint2* _
 
 // Candidate bits: vertex v is a candidate of variable u when its row holds
 // every out-predicate and its column every in-predicate u needs (Eq. 21).
-// One thread per vertex; each warp writes the whole word of its 32.
+// A warp takes 128 vertices at a time, four per lane (16-byte loads of
+// both masks); the 4-bit groups of 8 lanes are ORed into one word.
 __global__ void k_scan_eval(const uint32_t* __restrict__ mask_out,
                             const uint32_t* __restrict__ mask_in, uint32_t N, ScanDev sd,
                             uint32_t* __restrict__ bits, uint32_t words) {
     asm volatile("griddepcontrol.wait;" ::: "memory");   // the masks of k_scan
     const uint32_t lane = lane_id();
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v - lane < N;
-         v += gridDim.x * blockDim.x) {
-        const bool in = v < N;
-        const uint32_t mo = in ? __ldcs(mask_out + v) : 0u, mi = in ? __ldcs(mask_in + v) : 0u;
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g * 128 < N; g += warps) {
+        const uint32_t v = g * 128 + lane * 4;   // masks hold N + 8 words: the load stays inside
+        const uint4 mo = __ldcs(reinterpret_cast<const uint4*>(mask_out + v));
+        const uint4 mi = __ldcs(reinterpret_cast<const uint4*>(mask_in + v));
         for (uint32_t u = 0; u < sd.n_bvars; ++u) {
-            const uint32_t b = __ballot_sync(0xffffffffu, in && eval_bits(sd, mo, mi, u));
-            if (lane == 0) bits[(uint64_t)u * words + (v >> 5)] = b;
+            uint32_t nib = (eval_bits(sd, mo.x, mi.x, u) && v < N) |
+                           ((eval_bits(sd, mo.y, mi.y, u) && v + 1 < N) << 1) |
+                           ((eval_bits(sd, mo.z, mi.z, u) && v + 2 < N) << 2) |
+                           ((eval_bits(sd, mo.w, mi.w, u) && v + 3 < N) << 3);
+            uint32_t word = nib << (4 * (lane & 7));
+            word |= __shfl_xor_sync(0xffffffffu, word, 1);
+            word |= __shfl_xor_sync(0xffffffffu, word, 2);
+            word |= __shfl_xor_sync(0xffffffffu, word, 4);
+            const uint32_t wi = g * 4 + (lane >> 3);
+            if ((lane & 7) == 0 && wi < words) bits[(uint64_t)u * words + wi] = word;
         }
     }
 }
 
-// Workspace: mask_out (N + 8 words) | mask_in (N + 8 words) | status word.
+// Workspace: mask_out | mask_in (N + 128 words each, 16-byte aligned) |
+// status word.
+static uint64_t mask_words(uint32_t N) { return ((uint64_t)N + 128 + 3) & ~3ull; }
+
 size_t scan_work_bytes(const gs_graph* g) {
-    return 8ull * ((uint64_t)g->N + 8) + 512;
+    return 8ull * mask_words(g->N) + 512;
 }
 
 // Launch with programmatic stream serialization: the kernel may start
@@ -458,9 +471,9 @@ gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void
         sd.need_in[u] = spec.need_in[u];
     }
     uint32_t* mask_out = (uint32_t*)work;
-    uint32_t* mask_in = mask_out + ((uint64_t)g->N + 8);
+    uint32_t* mask_in = mask_out + mask_words(g->N);
     const bool own = status == nullptr;
-    if (own) status = mask_in + ((uint64_t)g->N + 8);
+    if (own) status = mask_in + mask_words(g->N);
     const uint32_t words = (g->N + 31) / 32;
     const int nb = g->n_blocks;
     k_scan_zero<<<nb, kThreads, 0, st>>>(g->out.ptr, g->out.items, g->out.n_items, g->in.ptr,
@@ -475,7 +488,7 @@ gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void
     else
         rc = launch_scan<uint8_t>(g, sd, mask_out, mask_in, status, w8, st);
     if (rc != GS_OK) return rc;
-    const uint32_t eb = (uint32_t)std::min<uint64_t>(((uint64_t)words * 32 + kThreads - 1) / kThreads, 1u << 20);
+    const uint32_t eb = std::min<uint32_t>((words + 31) / 32, (uint32_t)g->sm_count * 8);
     GS_CUDA(launch_dependent(k_scan_eval, dim3(std::max(1u, eb)), dim3(kThreads), 0, st,
                              (const uint32_t*)mask_out, (const uint32_t*)mask_in, g->N, sd, bits,
                              words));
