@@ -166,7 +166,8 @@ gs_status gs_result_stats(gs_result* r, float* device_ms, uint32_t* kernel_launc
  * counter and evaluates it on its own; answers of all queries share one
  * device pool. Plans that need the full triple scan, and queries that
  * outgrow one CTA's budget, are evaluated with the grid path of
- * gs_eval_query afterwards, on the same stream. Answers are identical to
+ * gs_eval_query on side streams of the graph (the former from the start,
+ * the latter after the batch kernel). Answers are identical to
  * gs_eval_query's.
  *
  *   plans        n plan pointers (host array; plans must outlive the batch)
@@ -177,6 +178,36 @@ gs_status gs_result_stats(gs_result* r, float* device_ms, uint32_t* kernel_launc
 typedef struct gs_batch gs_batch;
 gs_status gs_eval_batch(gs_graph* g, const gs_plan* const* plans, uint32_t n, void* cuda_stream,
                         gs_batch** out);
+
+/* Tunables of a batched evaluation; a zero field takes its default. */
+typedef struct {
+    uint32_t blocks_per_sm;  /* resident CTAs per SM of the batch kernel
+                                (0: as many as fit) */
+    uint32_t grid_streams;   /* streams on which grid-path queries run side by
+                                side (0: 4; at most 16) */
+    uint64_t cand_budget;    /* candidates a CTA takes at one level before
+                                handing its query to the grid path (0: 65,536) */
+    uint64_t row_budget;     /* answer rows a CTA writes before handing its
+                                query to the grid path (0: 65,536) */
+    uint64_t pool_bytes;     /* answer pool (0: min(4 GiB, free / 4), or
+                                GS_BATCH_POOL_BYTES) */
+} gs_batch_config;
+
+/* gs_eval_batch under cfg (NULL: all defaults). Grid-path queries run on
+ * up to cfg->grid_streams streams of the graph side by side and are joined
+ * before gs_batch_info returns. GS_EINVAL on a NULL graph, plan array or
+ * out pointer. */
+gs_status gs_eval_batch_cfg(gs_graph* g, const gs_plan* const* plans, uint32_t n,
+                            const gs_batch_config* cfg, void* cuda_stream, gs_batch** out);
+
+/* Autotuner: evaluates the n plans (a sample of the workload) under a fixed
+ * set of candidate configurations (CTAs per SM x candidate budget x row
+ * budget), each twice, and returns in *best the one with the smallest
+ * wall time from enqueue to the last answer count, which goes to
+ * *best_ms (may be NULL). Synchronizes cuda_stream; answers are discarded.
+ * Every configuration gives identical answers; only time differs. */
+gs_status gs_batch_autotune(gs_graph* g, const gs_plan* const* plans, uint32_t n,
+                            void* cuda_stream, gs_batch_config* best, float* best_ms);
 
 /* Non-blocking: *done = 1 once everything gs_eval_batch enqueued has
  * finished on the device (gs_batch_info then returns without waiting for the

@@ -30,7 +30,8 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_batch_fetch", "gs_batch_stats", "gs_free_batch", "gs_batch_poll",
             "gs_server_start", "gs_server_submit", "gs_server_poll", "gs_server_fetch",
             "gs_server_release", "gs_server_stats", "gs_server_stop",
-            "gs_scan_candidates_noalloc", "gs_noalloc_scratch_bytes"]
+            "gs_scan_candidates_noalloc", "gs_noalloc_scratch_bytes", "gs_eval_batch_cfg",
+            "gs_batch_autotune"]
 
 
 class GsError(RuntimeError):
@@ -41,6 +42,16 @@ class GsError(RuntimeError):
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class BatchConfig(ctypes.Structure):
+    """gs_batch_config: tunables of a batched evaluation (0 = default)."""
+    _fields_ = [("blocks_per_sm", ctypes.c_uint32), ("grid_streams", ctypes.c_uint32),
+                ("cand_budget", ctypes.c_uint64), ("row_budget", ctypes.c_uint64),
+                ("pool_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 class _Allocator(ctypes.Structure):
@@ -109,6 +120,8 @@ def load_library(path: str | None = None):
         "gs_scan_candidates": [vp, vp, vp, u32, vp, vp],
         "gs_scan_candidates_noalloc": [vp, vp, vp, u32, vp, vp],
         "gs_eval_batch": [vp, vp, u32, vp, P(vp)],
+        "gs_eval_batch_cfg": [vp, vp, u32, vp, vp, P(vp)],
+        "gs_batch_autotune": [vp, vp, u32, vp, vp, P(ctypes.c_float)],
         "gs_batch_info": [vp, vp, P(u64)],
         "gs_batch_fetch": [vp, u32, vp, u64, i32, i32],
         "gs_batch_stats": [vp, P(ctypes.c_float), P(u32), P(u32)],
@@ -224,14 +237,30 @@ class Graph:
         finally:
             r.close()
 
-    def eval_batch(self, plans, stream=None) -> "Batch":
-        """Evaluate many plans (or pattern arrays) in one persistent launch."""
+    def eval_batch(self, plans, stream=None, config: "BatchConfig | None" = None) -> "Batch":
+        """Evaluate many plans (or pattern arrays) in one persistent launch,
+        under `config` (a BatchConfig; None: defaults)."""
         plans = [p if isinstance(p, Plan) else self.plan(p) for p in plans]
         arr = (ctypes.c_void_p * max(1, len(plans)))(*[p._h.value for p in plans])
         h = ctypes.c_void_p()
-        _check(_lib.gs_eval_batch(self._h, arr, len(plans), _stream_handle(stream),
-                                  ctypes.byref(h)))
+        if config is None:
+            _check(_lib.gs_eval_batch(self._h, arr, len(plans), _stream_handle(stream),
+                                      ctypes.byref(h)))
+        else:
+            _check(_lib.gs_eval_batch_cfg(self._h, arr, len(plans), ctypes.byref(config),
+                                          _stream_handle(stream), ctypes.byref(h)))
         return Batch(h, plans)
+
+    def autotune_batch(self, plans, stream=None):
+        """The batch configuration the native autotuner picks for these plans
+        (a sample of the workload) and its wall time in ms."""
+        plans = [p if isinstance(p, Plan) else self.plan(p) for p in plans]
+        arr = (ctypes.c_void_p * max(1, len(plans)))(*[p._h.value for p in plans])
+        cfg = BatchConfig()
+        ms = ctypes.c_float()
+        _check(_lib.gs_batch_autotune(self._h, arr, len(plans), _stream_handle(stream),
+                                      ctypes.byref(cfg), ctypes.byref(ms)))
+        return cfg, float(ms.value)
 
     def scan(self, preds, dirs, out=None, stream=None):
         """Eq. 17 / Eq. 21 on its own: a torch int32 tensor of ceil(N/32)

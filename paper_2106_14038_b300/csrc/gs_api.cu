@@ -428,6 +428,7 @@ void gs_free_graph(gs_graph* g) {
     cudaDeviceSynchronize();
     free_store(g, nullptr);
     cudaDeviceSynchronize();
+    for (int i = 0; i < g->n_side; ++i) cudaStreamDestroy(g->side[i]);
     delete g;
 }
 

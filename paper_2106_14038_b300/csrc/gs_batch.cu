@@ -3,10 +3,12 @@
 // single-block record into one staging buffer (one copy to the device),
 // launches one CTA per resident slot; every CTA pulls queries from a device
 // counter and evaluates them in its own workspace, writing answers into a
-// shared pool. Queries that need the full triple scan, do not fit a record,
-// or outgrow the per-CTA budgets run on the grid path afterwards, each as
-// an ordinary result.
+// shared pool. Queries that need the full triple scan or do not fit a
+// record run on the grid path from the start, and queries that outgrow the
+// per-CTA budgets after the batch kernel; grid-path queries run side by
+// side on the graph's side streams, each as an ordinary result.
 #include <algorithm>
+#include <chrono>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -39,19 +41,57 @@ struct gs_batch {
     int blocks = 0;
     cudaEvent_t ev_enq = nullptr;          // after everything gs_eval_batch enqueued
     bool ready = false;
+    gs_batch_config cfg{};                 // with every default filled in
+    uint32_t next_side = 0;                // round robin over the side streams
 };
 
 namespace {
 
 constexpr uint64_t kBatchCand = 1ull << 16;
-constexpr uint64_t kBatchRows = 1ull << 20;
+constexpr uint64_t kBatchRows = 1ull << 16;
 constexpr uint64_t kSlotBytes = 24ull << 20;
 constexpr uint64_t kPoolDefault = 4ull << 30;
+constexpr uint32_t kGridStreams = 4;
 
-int batch_blocks(const gs_graph* g) {
-    int per_sm = batch_blocks_per_sm();
-    if (const char* e = getenv("GS_BATCH_BLOCKS_PER_SM")) per_sm = std::max(1, std::min(per_sm, atoi(e)));
-    return g->sm_count * per_sm;
+// Side stream i of the graph, created on first use.
+gs_status side_stream(gs_graph* g, uint32_t i, cudaStream_t* out) {
+    i %= 16;
+    while (g->n_side <= (int)i) {
+        GS_CUDA(cudaStreamCreateWithFlags(&g->side[g->n_side], cudaStreamNonBlocking));
+        g->n_side++;
+    }
+    *out = g->side[i];
+    return GS_OK;
+}
+
+// The grid path for plan on the batch's next side stream.
+gs_status grid_query(gs_batch* b, const gs_plan* plan, gs_result** r) {
+    cudaStream_t st = nullptr;
+    gs_status rc = side_stream(b->g, b->next_side++ % b->cfg.grid_streams, &st);
+    if (rc != GS_OK) return rc;
+    return eval_query_path(b->g, plan, (void*)st, 1, r);
+}
+
+gs_batch_config resolve(const gs_graph* g, const gs_batch_config* c) {
+    gs_batch_config r = c ? *c : gs_batch_config{};
+    const int fit = batch_blocks_per_sm();
+    if (r.blocks_per_sm == 0) {
+        r.blocks_per_sm = (uint32_t)fit;
+        if (const char* e = getenv("GS_BATCH_BLOCKS_PER_SM")) r.blocks_per_sm = (uint32_t)std::max(1, atoi(e));
+    }
+    r.blocks_per_sm = std::max(1u, std::min(r.blocks_per_sm, (uint32_t)fit));
+    if (r.grid_streams == 0) r.grid_streams = kGridStreams;
+    r.grid_streams = std::min(r.grid_streams, 16u);
+    if (r.cand_budget == 0) r.cand_budget = kBatchCand;
+    if (r.row_budget == 0) r.row_budget = kBatchRows;
+    if (r.pool_bytes == 0) {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        r.pool_bytes = std::min<uint64_t>(kPoolDefault, free_b / 4);
+        if (const char* e = getenv("GS_BATCH_POOL_BYTES")) r.pool_bytes = strtoull(e, nullptr, 10);
+    }
+    (void)g;
+    return r;
 }
 
 gs_status finish(gs_batch* b) {
@@ -63,12 +103,12 @@ gs_status finish(gs_batch* b) {
         GS_CUDA(cudaMemcpy(kr.data(), b->res_dev, sizeof(BatchResult) * nk, cudaMemcpyDeviceToHost));
         for (uint32_t i = 0; i < nk; ++i) b->res[b->kidx[i]] = kr[i];
     }
-    // grid path for the queries the kernel handed back
+    // grid path for the queries the kernel handed back, side by side
     for (uint32_t q = 0; q < b->n; ++q) {
         if (!b->in_kernel[q] || b->res[q].status == 0) continue;
         b->escalated++;
         gs_result* r = nullptr;
-        gs_status rc = eval_query_path(b->g, b->plans[q], (void*)b->st, 1, &r);
+        gs_status rc = grid_query(b, b->plans[q], &r);
         if (rc != GS_OK) return rc;
         b->sub[q] = r;
     }
@@ -110,13 +150,18 @@ extern "C" {
 
 gs_status gs_eval_batch(gs_graph* g, const gs_plan* const* plans, uint32_t n, void* cuda_stream,
                         gs_batch** out) {
-    return eval_batch_ex(g, plans, n, cuda_stream, 0, 0, out);
+    return eval_batch_ex(g, plans, n, cuda_stream, nullptr, 0, out);
+}
+
+gs_status gs_eval_batch_cfg(gs_graph* g, const gs_plan* const* plans, uint32_t n,
+                            const gs_batch_config* cfg, void* cuda_stream, gs_batch** out) {
+    return eval_batch_ex(g, plans, n, cuda_stream, cfg, 0, out);
 }
 
 }  // extern "C"
 
 gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n, void* cuda_stream,
-                            int max_blocks, uint64_t pool_bytes, gs_batch** out) {
+                            const gs_batch_config* cfg, int max_blocks, gs_batch** out) {
     if (!g || !out || (n && !plans)) { set_error("gs_eval_batch: NULL argument"); return GS_EINVAL; }
     *out = nullptr;
     for (uint32_t q = 0; q < n; ++q) {
@@ -131,6 +176,7 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
     b->g = g;
     b->st = (cudaStream_t)cuda_stream;
     b->n = n;
+    b->cfg = resolve(g, cfg);
     b->plans.assign(plans, plans + n);
     b->n_vars.resize(n);
     b->in_kernel.assign(n, 0);
@@ -169,16 +215,12 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
     for (uint32_t i = 0; i < n_in; ++i) pack_record(plans[b->kidx[i]], b->staging + off[i]);
     std::memcpy(b->staging + total, off.data(), off_bytes);
     b->dev = (uint8_t*)g->alloc.get(dev_bytes, b->st);
-    int blocks = batch_blocks(g);
+    int blocks = g->sm_count * (int)b->cfg.blocks_per_sm;
     if (max_blocks > 0) blocks = std::min(blocks, max_blocks);
     blocks = std::max(1, std::min<int>(blocks, (int)std::max<uint32_t>(1, n_in)));
     b->blocks = blocks;
     b->slots = (uint8_t*)g->alloc.get(kSlotBytes * blocks, b->st);
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    b->pool_bytes = std::min<uint64_t>(kPoolDefault, free_b / 4);
-    if (pool_bytes) b->pool_bytes = pool_bytes;
-    if (const char* e = getenv("GS_BATCH_POOL_BYTES")) b->pool_bytes = strtoull(e, nullptr, 10);
+    b->pool_bytes = b->cfg.pool_bytes;
     b->pool = (uint8_t*)g->alloc.get(std::max<uint64_t>(b->pool_bytes, 256), b->st);
     if (!b->dev || !b->slots || !b->pool) {
         set_error("gs_eval_batch: out of device memory");
@@ -208,14 +250,15 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
         B.pool_top = (unsigned long long*)(counters + 2);
         B.next = counters;
         B.res = b->res_dev;
-        B.cand_budget = kBatchCand;
-        B.row_budget = kBatchRows;
+        B.cand_budget = b->cfg.cand_budget;
+        B.row_budget = b->cfg.row_budget;
         rc = enqueue_batch(B, blocks, b->st);
         b->launches = 1;
     }
-    // plans outside the record format go straight to the grid path (same stream)
+    // plans outside the record format go straight to the grid path, beside
+    // the batch kernel
     for (uint32_t q = 0; q < n && rc == GS_OK; ++q)
-        if (!b->in_kernel[q]) rc = eval_query_path(g, plans[q], (void*)b->st, 1, &b->sub[q]);
+        if (!b->in_kernel[q]) rc = grid_query(b, plans[q], &b->sub[q]);
     if (rc == GS_OK) {
         cudaError_t e2 = cudaEventRecord(b->ev_enq, b->st);
         if (e2 != cudaSuccess) rc = cuda_fail(e2, "gs_eval_batch");
@@ -305,3 +348,61 @@ gs_status gs_batch_stats(gs_batch* b, float* device_ms, uint32_t* kernel_launche
 void gs_free_batch(gs_batch* b) { release(b); }
 
 }  // extern "C"
+
+namespace {
+
+// Wall time of one batched evaluation of the plans under cfg (enqueue to
+// the last answer count), or a negative value on failure.
+double time_batch(gs_graph* g, const gs_plan* const* plans, uint32_t n, const gs_batch_config& cfg,
+                  void* stream, gs_status* rc) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    gs_batch* b = nullptr;
+    *rc = eval_batch_ex(g, plans, n, stream, &cfg, 0, &b);
+    if (*rc != GS_OK) return -1.0;
+    *rc = gs_batch_info(b, nullptr, nullptr);
+    const auto t1 = std::chrono::steady_clock::now();
+    gs_free_batch(b);
+    if (*rc != GS_OK) return -1.0;
+    return std::chrono::duration<double, std::milli>(t1 - t0).count();
+}
+
+}  // namespace
+
+extern "C" gs_status gs_batch_autotune(gs_graph* g, const gs_plan* const* plans, uint32_t n,
+                                       void* cuda_stream, gs_batch_config* best, float* best_ms) {
+    if (!g || !best || (n && !plans)) { set_error("gs_batch_autotune: NULL argument"); return GS_EINVAL; }
+    const uint32_t fit = (uint32_t)batch_blocks_per_sm();
+    std::vector<uint32_t> bps = {1u, 2u, fit};
+    std::sort(bps.begin(), bps.end());
+    bps.erase(std::unique(bps.begin(), bps.end()), bps.end());
+    bps.erase(std::remove_if(bps.begin(), bps.end(), [&](uint32_t x) { return x > fit; }), bps.end());
+    const uint64_t cands[] = {1ull << 12, 1ull << 16};
+    const uint64_t rows[] = {1ull << 12, 1ull << 16, 1ull << 20};
+    gs_batch_config cfg{};
+    gs_status rc = GS_OK;
+    time_batch(g, plans, n, cfg, cuda_stream, &rc);   // warm-up (allocator, streams)
+    if (rc != GS_OK) return rc;
+    double best_t = -1.0;
+    for (uint32_t bp : bps)
+        for (uint64_t cb : cands)
+            for (uint64_t rb : rows) {
+                cfg = gs_batch_config{};
+                cfg.blocks_per_sm = bp;
+                cfg.cand_budget = cb;
+                cfg.row_budget = rb;
+                double t = -1.0;
+                for (int rep = 0; rep < 2; ++rep) {
+                    const double x = time_batch(g, plans, n, cfg, cuda_stream, &rc);
+                    if (rc != GS_OK) return rc;
+                    if (t < 0 || x < t) t = x;
+                }
+                if (best_t < 0 || t < best_t) {
+                    best_t = t;
+                    *best = cfg;
+                }
+            }
+    best->grid_streams = kGridStreams;
+    if (best_ms) *best_ms = (float)best_t;
+    return GS_OK;
+}

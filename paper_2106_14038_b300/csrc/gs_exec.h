@@ -97,10 +97,10 @@ gs_status sort_rows_on_device(const gs_graph* g, const int32_t* rows, uint64_t n
                               int32_t* out, cudaStream_t st);
 gs_status eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
                           gs_result** out);
-// gs_eval_batch with at most max_blocks CTAs (0: one per resident slot) and a
-// pool of pool_bytes (0: the default).
+// gs_eval_batch with the tunables of cfg (NULL or zero fields: defaults)
+// and at most max_blocks CTAs (0: no cap).
 gs_status eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n, void* cuda_stream,
-                        int max_blocks, uint64_t pool_bytes, gs_batch** out);
+                        const gs_batch_config* cfg, int max_blocks, gs_batch** out);
 uint64_t batch_device_bytes(const gs_batch* b);
 
 uint64_t host_level_off(const uint64_t* n, int l);

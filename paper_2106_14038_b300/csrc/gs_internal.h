@@ -91,6 +91,10 @@ struct gs_graph {
     int sm_count = 148;
     int n_blocks = 592;
     int device = 0;
+    // streams on which batched evaluations run their grid-path queries
+    // side by side (created on first use, destroyed with the graph)
+    cudaStream_t side[16] = {};
+    int n_side = 0;
 };
 
 namespace gs {

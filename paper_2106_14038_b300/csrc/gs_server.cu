@@ -146,8 +146,10 @@ void worker_loop(gs_server* s) {
                     f->plans.push_back(t.plan);
                 }
                 f->refs = (int)take;
+                gs_batch_config bc{};
+                bc.pool_bytes = s->cfg.pool_bytes_per_query * take;
                 gs_status rc = eval_batch_ex(s->g, f->plans.data(), take, (void*)s->streams[st],
-                                             0, s->cfg.pool_bytes_per_query * take, &f->b);
+                                             &bc, 0, &f->b);
                 if (rc != GS_OK) {
                     for (uint64_t id : f->tickets) {
                         Ticket& t = s->tickets[id];

@@ -311,6 +311,49 @@ def test_batch_equals_oracle(rmat14, monkeypatch):
     b.close()
 
 
+def _batch_pats(w, s, p, o, seed):
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    pats = [q.patterns for q in rdfgen.queries(w, sm)]
+    rng = np.random.default_rng(seed)
+    for i in range(24):
+        sh = [rdfgen.star(2), rdfgen.chain(2), rdfgen.cycle(3), rdfgen.snowflake([1, 1])][i % 4]
+        sh.const = [int(rng.integers(0, sh.n_v))]
+        pats.append(sm.sample(sh, 99, 100 + i, 1e5).patterns)
+    pats.append(np.array([(-1, 1, -2)], np.int64))        # constant-free: grid path
+    return pats
+
+
+@pytest.mark.parametrize("cfg", [dict(blocks_per_sm=1, cand_budget=16, row_budget=16),
+                                 dict(row_budget=1 << 20, grid_streams=1),
+                                 dict(blocks_per_sm=2, grid_streams=16, cand_budget=1 << 12)])
+def test_batch_configs_equal_oracle(rmat14, cfg):
+    # tiny budgets hand most queries to the grid path (run on side streams);
+    # every configuration gives the oracle's answers
+    w, (s, p, o), g, ix = rmat14
+    pats = _batch_pats(w, s, p, o, 8)
+    b = g.eval_batch(pats, config=gs.BatchConfig(**cfg))
+    rows = b.rows()
+    _, _, esc = b.stats()
+    if cfg.get("row_budget") == 16:
+        assert esc > 0
+    for i, pt in enumerate(pats):
+        want = ix.eval(pt, threads=4)
+        assert int(rows[i]) == len(want), (cfg, i)
+        assert np.array_equal(b.fetch(i), want), (cfg, i)
+    b.close()
+
+
+def test_batch_autotune_picks_a_working_config(rmat14):
+    w, (s, p, o), g, ix = rmat14
+    pats = _batch_pats(w, s, p, o, 9)
+    cfg, ms = g.autotune_batch(pats)
+    assert ms > 0 and cfg.blocks_per_sm >= 1 and cfg.cand_budget > 0 and cfg.row_budget > 0
+    b = g.eval_batch(pats, config=cfg)
+    for i, pt in enumerate(pats):
+        assert np.array_equal(b.fetch(i), ix.eval(pt, threads=4)), i
+    b.close()
+
+
 def test_batch_small_pool_hands_back(rmat14, monkeypatch):
     # a pool too small for most answers: those queries go to the grid path
     w, (s, p, o), g, ix = rmat14
