@@ -234,20 +234,28 @@ void gs_free_batch(gs_batch* b);
 /* ------------------------------------------------------------------ */
 /* Serving loop (continuous batching). The server keeps the graph resident
  * and owns a worker thread and a pool of CUDA streams. Submitted plans wait
- * in arrival order; the worker admits the waiting plans into a batch (as in
- * gs_eval_batch) while the batch's device-memory estimate (per-CTA
+ * in arrival order; when the device is idle, when max_batch / 8 plans
+ * wait, or when the oldest has waited max_wait_us, the worker admits the
+ * waiting plans into a batch (as in gs_eval_batch) while the batch's
+ * device-memory estimate (per-CTA
  * workspaces plus pool_bytes_per_query per query) fits the memory budget
  * together with the batches in flight, and a stream is free. Batches
- * admitted while others run overlap on the device. Answers are identical to
- * gs_eval_query's; they stay on the device until the ticket is released.
+ * admitted while others run overlap on the device; queries a batch hands
+ * to the grid path run on the graph's side streams without holding up the
+ * worker. Answers are identical to gs_eval_query's; they stay on the
+ * device until the ticket is released.
  * Submit / poll / fetch / release may be called from any host thread. */
 typedef struct gs_server gs_server;
 typedef struct {
     uint32_t max_batch;              /* queries per batch (0: 1024) */
     uint32_t n_streams;              /* batches in flight (0: 4) */
     uint64_t memory_budget;          /* bytes of device memory (0: 40 GiB) */
-    uint32_t max_wait_us;            /* worker idle wait (0: 50) */
+    uint32_t max_wait_us;            /* while batches run, the longest a
+                                        queued query waits for more arrivals
+                                        before it starts a batch (0: 200) */
     uint64_t pool_bytes_per_query;   /* answer pool share (0: 16 MiB) */
+    gs_batch_config batch;           /* tunables of every batch (zero fields:
+                                        defaults; pool_bytes is ignored) */
 } gs_server_config;
 
 gs_status gs_server_start(gs_graph* g, const gs_server_config* cfg, gs_server** out);
@@ -267,6 +275,18 @@ gs_status gs_server_stats(gs_server* s, uint64_t* completed, uint64_t* batches,
                           uint64_t* peak_bytes);
 /* Finish the queued work, free everything. */
 void gs_server_stop(gs_server* s);
+
+/* Load replay (a measuring aid, no counterpart in the paper): submits n
+ * queries, query i being plans[i % n_plans], each at arrival_s[i] seconds
+ * after the call starts (non-decreasing), from the calling thread; polls
+ * and releases them as they finish. latency_us[i] (may be NULL) receives
+ * the time from the scheduled arrival to completion as the server's worker
+ * saw it, done_s[i] (may be NULL) the completion time since the call
+ * started. Returns when every query has finished; GS_ETIMEOUT if that
+ * takes longer than timeout_s; a failed query's status otherwise. */
+gs_status gs_server_replay(gs_server* s, const gs_plan* const* plans, uint32_t n_plans,
+                           const double* arrival_s, uint64_t n, double timeout_s,
+                           double* latency_us, double* done_s);
 
 /* ------------------------------------------------------------------ */
 /* One grouped predicate selection on its own (Eq. 17, Eq. 21):

@@ -31,7 +31,7 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_server_start", "gs_server_submit", "gs_server_poll", "gs_server_fetch",
             "gs_server_release", "gs_server_stats", "gs_server_stop",
             "gs_scan_candidates_noalloc", "gs_noalloc_scratch_bytes", "gs_eval_batch_cfg",
-            "gs_batch_autotune"]
+            "gs_batch_autotune", "gs_server_replay"]
 
 
 class GsError(RuntimeError):
@@ -122,6 +122,7 @@ def load_library(path: str | None = None):
         "gs_eval_batch": [vp, vp, u32, vp, P(vp)],
         "gs_eval_batch_cfg": [vp, vp, u32, vp, vp, P(vp)],
         "gs_batch_autotune": [vp, vp, u32, vp, vp, P(ctypes.c_float)],
+        "gs_server_replay": [vp, vp, u32, vp, u64, ctypes.c_double, vp, vp],
         "gs_batch_info": [vp, vp, P(u64)],
         "gs_batch_fetch": [vp, u32, vp, u64, i32, i32],
         "gs_batch_stats": [vp, P(ctypes.c_float), P(u32), P(u32)],
@@ -384,15 +385,17 @@ class Batch:
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_uint32), ("n_streams", ctypes.c_uint32),
                 ("memory_budget", ctypes.c_uint64), ("max_wait_us", ctypes.c_uint32),
-                ("pool_bytes_per_query", ctypes.c_uint64)]
+                ("pool_bytes_per_query", ctypes.c_uint64), ("batch", BatchConfig)]
 
 
 class Server:
     """Continuous-batching server over a resident graph (gs_server_*)."""
 
     def __init__(self, graph: Graph, max_batch: int = 0, n_streams: int = 0,
-                 memory_budget: int = 0, max_wait_us: int = 0, pool_bytes_per_query: int = 0):
-        cfg = _ServerConfig(max_batch, n_streams, memory_budget, max_wait_us, pool_bytes_per_query)
+                 memory_budget: int = 0, max_wait_us: int = 0, pool_bytes_per_query: int = 0,
+                 batch: "BatchConfig | None" = None):
+        cfg = _ServerConfig(max_batch, n_streams, memory_budget, max_wait_us, pool_bytes_per_query,
+                            batch if batch is not None else BatchConfig())
         h = ctypes.c_void_p()
         _check(_lib.gs_server_start(graph._h, ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
@@ -433,6 +436,18 @@ class Server:
         a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         _check(_lib.gs_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return int(a.value), int(b.value), int(c.value)
+
+    def replay(self, plans, arrival_s, timeout_s: float = 120.0):
+        """Native load replay: query i is plans[i % len(plans)], submitted at
+        arrival_s[i] seconds; returns (latency_us, done_s) arrays."""
+        arr = (ctypes.c_void_p * max(1, len(plans)))(*[p._h.value for p in plans])
+        at = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        lat = np.zeros(len(at))
+        done = np.zeros(len(at))
+        _check(_lib.gs_server_replay(self._h, arr, len(plans), at.ctypes.data_as(ctypes.c_void_p),
+                                     len(at), float(timeout_s), lat.ctypes.data_as(ctypes.c_void_p),
+                                     done.ctypes.data_as(ctypes.c_void_p)))
+        return lat, done
 
     def stop(self):
         if getattr(self, "_h", None):

@@ -279,6 +279,38 @@ gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint
 
 }  // extern "C"
 
+gs_status gs::result_compact(gs_result* r) {
+    gs_status rc = wait_result(r);
+    if (rc != GS_OK) return rc;
+    const uint64_t bytes = std::max<uint64_t>(16, 4ull * r->rows * (uint64_t)r->plan.n_vars);
+    if (bytes >= r->arena_bytes / 2 && !r->bits && !r->work && !r->lists) return GS_OK;
+    uint8_t* keep = (uint8_t*)r->g->alloc.get(bytes, r->st);
+    if (!keep) return GS_OK;   // keep the arena: the answers stay where they are
+    if (r->rows)
+        GS_CUDA(cudaMemcpyAsync(keep, r->arena + r->out_off, 4ull * r->rows * r->plan.n_vars,
+                                cudaMemcpyDeviceToDevice, r->st));
+    r->g->alloc.put(r->arena, r->st);
+    r->g->alloc.put(r->bits, r->st);
+    r->g->alloc.put(r->work, r->st);
+    r->g->alloc.put(r->lists, r->st);
+    r->bits = nullptr;
+    r->work = nullptr;
+    r->lists = nullptr;
+    r->arena = keep;
+    r->arena_bytes = bytes;
+    r->out_off = 0;
+    return GS_OK;
+}
+
+gs_status gs::result_ready(gs_result* r, int* done) {
+    if (r->ready) { *done = 1; return GS_OK; }
+    cudaError_t e = cudaEventQuery(r->ev1);
+    if (e == cudaErrorNotReady) { *done = 0; return GS_OK; }
+    if (e != cudaSuccess) return cuda_fail(e, "gs_eval_query");
+    *done = 1;
+    return GS_OK;
+}
+
 gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
                               gs_result** out) {
     if (!g || !plan || !out) { set_error("gs_eval_query: NULL argument"); return GS_EINVAL; }

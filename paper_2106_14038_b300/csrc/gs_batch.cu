@@ -35,7 +35,7 @@ struct gs_batch {
     BatchResult* res_dev = nullptr;
     std::vector<BatchResult> res;
     std::vector<gs_result*> sub;           // grid-path results
-    uint8_t* staging = nullptr;            // pinned host
+    std::vector<uint8_t> staging;          // packed records and offsets (host)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     uint32_t launches = 0, escalated = 0;
     int blocks = 0;
@@ -43,13 +43,25 @@ struct gs_batch {
     bool ready = false;
     gs_batch_config cfg{};                 // with every default filled in
     uint32_t next_side = 0;                // round robin over the side streams
+    uint64_t slot_bytes = 0;
+    int stage = 0;                         // 0: batch kernel enqueued, 1: its results read
+    std::vector<uint32_t> todo;            // queries waiting for the grid path
+    std::vector<uint32_t> active;          // queries on the grid path now
+    size_t todo_next = 0;
 };
 
 namespace {
 
 constexpr uint64_t kBatchCand = 1ull << 16;
 constexpr uint64_t kBatchRows = 1ull << 16;
-constexpr uint64_t kSlotBytes = 24ull << 20;
+constexpr uint64_t kSlotMax = 24ull << 20;
+
+// Workspace of one CTA: the control block and up to 12 levels of
+// cand_budget nodes with their scratch; a query that needs more is handed
+// to the grid path.
+uint64_t slot_bytes_for(uint64_t cand_budget) {
+    return std::min<uint64_t>(kSlotMax, (256ull << 10) + cand_budget * 160);
+}
 constexpr uint64_t kPoolDefault = 4ull << 30;
 constexpr uint32_t kGridStreams = 4;
 
@@ -94,38 +106,74 @@ gs_batch_config resolve(const gs_graph* g, const gs_batch_config* c) {
     return r;
 }
 
-gs_status finish(gs_batch* b) {
-    if (b->ready) return GS_OK;
-    GS_CUDA(cudaStreamSynchronize(b->st));
+// Start grid-path queries from the to-do list while fewer than
+// grid_streams run (bounds the workspaces held at once).
+gs_status launch_todo(gs_batch* b) {
+    while (b->active.size() < b->cfg.grid_streams && b->todo_next < b->todo.size()) {
+        const uint32_t q = b->todo[b->todo_next++];
+        gs_result* r = nullptr;
+        gs_status rc = grid_query(b, b->plans[q], &r);
+        if (rc != GS_OK) return rc;
+        b->sub[q] = r;
+        b->active.push_back(q);
+    }
+    return GS_OK;
+}
+
+// A grid-path query finished: its count, then its answers compacted.
+gs_status retire(gs_batch* b, uint32_t q) {
+    uint64_t rows = 0;
+    gs_status rc = gs_result_info(b->sub[q], &rows, nullptr);
+    if (rc != GS_OK) return rc;
+    uint32_t nl = 0;
+    gs_result_stats(b->sub[q], nullptr, &nl);
+    b->launches += nl;
+    b->res[q].rows = rows;
+    return result_compact(b->sub[q]);
+}
+
+// The batch kernel has finished: read its results and queue the queries it
+// handed back.
+gs_status collect_kernel(gs_batch* b) {
     const uint32_t nk = (uint32_t)b->kidx.size();
     if (b->res_dev && nk) {
         std::vector<BatchResult> kr(nk);
         GS_CUDA(cudaMemcpy(kr.data(), b->res_dev, sizeof(BatchResult) * nk, cudaMemcpyDeviceToHost));
         for (uint32_t i = 0; i < nk; ++i) b->res[b->kidx[i]] = kr[i];
     }
-    // grid path for the queries the kernel handed back, side by side
     for (uint32_t q = 0; q < b->n; ++q) {
         if (!b->in_kernel[q] || b->res[q].status == 0) continue;
         b->escalated++;
-        gs_result* r = nullptr;
-        gs_status rc = grid_query(b, b->plans[q], &r);
-        if (rc != GS_OK) return rc;
-        b->sub[q] = r;
+        b->todo.push_back(q);
     }
-    for (uint32_t q = 0; q < b->n; ++q) {
-        if (!b->sub[q]) continue;
-        uint64_t rows = 0;
-        gs_status rc = gs_result_info(b->sub[q], &rows, nullptr);
-        if (rc != GS_OK) return rc;
-        uint32_t nl = 0;
-        gs_result_stats(b->sub[q], nullptr, &nl);
-        b->launches += nl;
-        b->res[q].rows = rows;
-    }
+    b->g->alloc.put(b->slots, b->st);   // the CTA workspaces are done
+    b->slots = nullptr;
+    b->stage = 1;
+    return launch_todo(b);
+}
+
+gs_status all_done(gs_batch* b) {
     GS_CUDA(cudaEventRecord(b->ev1, b->st));
     GS_CUDA(cudaEventSynchronize(b->ev1));
     b->ready = true;
     return GS_OK;
+}
+
+gs_status finish(gs_batch* b) {
+    if (b->ready) return GS_OK;
+    if (b->stage == 0) {
+        GS_CUDA(cudaStreamSynchronize(b->st));
+        gs_status rc = collect_kernel(b);
+        if (rc != GS_OK) return rc;
+    }
+    while (!b->active.empty()) {
+        const uint32_t q = b->active.front();
+        b->active.erase(b->active.begin());
+        gs_status rc = retire(b, q);
+        if (rc == GS_OK) rc = launch_todo(b);
+        if (rc != GS_OK) return rc;
+    }
+    return all_done(b);
 }
 
 void release(gs_batch* b) {
@@ -137,7 +185,6 @@ void release(gs_batch* b) {
         b->g->alloc.put(b->slots, b->st);
         b->g->alloc.put(b->pool, b->st);
     }
-    if (b->staging) cudaFreeHost(b->staging);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     if (b->ev_enq) cudaEventDestroy(b->ev_enq);
@@ -206,20 +253,16 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
     }
     const uint64_t off_bytes = 8ull * n_in, res_bytes = sizeof(BatchResult) * (uint64_t)n_in;
     const uint64_t dev_bytes = total + off_bytes + res_bytes + 256;
-    if (cudaMallocHost(&b->staging, total + off_bytes + 16) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("gs_eval_batch: cannot allocate pinned staging memory");
-        release(b);
-        return GS_ENOMEM;
-    }
-    for (uint32_t i = 0; i < n_in; ++i) pack_record(plans[b->kidx[i]], b->staging + off[i]);
-    std::memcpy(b->staging + total, off.data(), off_bytes);
+    b->staging.assign(total + off_bytes + 16, 0);
+    for (uint32_t i = 0; i < n_in; ++i) pack_record(plans[b->kidx[i]], b->staging.data() + off[i]);
+    std::memcpy(b->staging.data() + total, off.data(), off_bytes);
     b->dev = (uint8_t*)g->alloc.get(dev_bytes, b->st);
     int blocks = g->sm_count * (int)b->cfg.blocks_per_sm;
     if (max_blocks > 0) blocks = std::min(blocks, max_blocks);
     blocks = std::max(1, std::min<int>(blocks, (int)std::max<uint32_t>(1, n_in)));
     b->blocks = blocks;
-    b->slots = (uint8_t*)g->alloc.get(kSlotBytes * blocks, b->st);
+    b->slot_bytes = slot_bytes_for(b->cfg.cand_budget);
+    b->slots = (uint8_t*)g->alloc.get(b->slot_bytes * blocks, b->st);
     b->pool_bytes = b->cfg.pool_bytes;
     b->pool = (uint8_t*)g->alloc.get(std::max<uint64_t>(b->pool_bytes, 256), b->st);
     if (!b->dev || !b->slots || !b->pool) {
@@ -230,7 +273,8 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
     gs_status rc = GS_OK;
     cudaError_t e = cudaEventRecord(b->ev0, b->st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->dev, b->staging, total + off_bytes, cudaMemcpyHostToDevice, b->st);
+        // from pageable memory: the call returns once the bytes are staged
+        e = cudaMemcpyAsync(b->dev, b->staging.data(), total + off_bytes, cudaMemcpyHostToDevice, b->st);
     b->res_dev = (BatchResult*)(b->dev + total + off_bytes);
     uint32_t* counters = (uint32_t*)(b->dev + total + off_bytes + res_bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 64, b->st);
@@ -243,7 +287,7 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
         B.rec_off = (const uint64_t*)(b->dev + total);
         B.n = n_in;
         B.slots = b->slots;
-        B.slot_bytes = kSlotBytes;
+        B.slot_bytes = b->slot_bytes;
         (void)0;
         B.pool = b->pool;
         B.pool_bytes = b->pool_bytes;
@@ -257,8 +301,9 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
     }
     // plans outside the record format go straight to the grid path, beside
     // the batch kernel
-    for (uint32_t q = 0; q < n && rc == GS_OK; ++q)
-        if (!b->in_kernel[q]) rc = grid_query(b, plans[q], &b->sub[q]);
+    for (uint32_t q = 0; q < n; ++q)
+        if (!b->in_kernel[q]) b->todo.push_back(q);
+    if (rc == GS_OK) rc = launch_todo(b);
     if (rc == GS_OK) {
         cudaError_t e2 = cudaEventRecord(b->ev_enq, b->st);
         if (e2 != cudaSuccess) rc = cuda_fail(e2, "gs_eval_batch");
@@ -269,7 +314,44 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
 }
 
 uint64_t gs::batch_device_bytes(const gs_batch* b) {
-    return kSlotBytes * (uint64_t)b->blocks + b->pool_bytes;
+    return b->slot_bytes * (uint64_t)b->blocks + b->pool_bytes;
+}
+
+uint64_t gs::batch_estimate(const gs_graph* g, const gs_batch_config* cfg, uint32_t n,
+                            uint64_t pool_bytes) {
+    const gs_batch_config c = resolve(g, cfg);
+    const uint64_t blocks = std::min<uint64_t>(n, (uint64_t)g->sm_count * c.blocks_per_sm);
+    // plus the grid-path queries it may run at once (workspace and scan masks)
+    const uint64_t grid = (uint64_t)c.grid_streams * ((512ull << 20) + scan_work_bytes(g));
+    return blocks * slot_bytes_for(c.cand_budget) + pool_bytes + grid;
+}
+
+gs_status gs::batch_advance(gs_batch* b, int* done) {
+    *done = 0;
+    if (b->ready) { *done = 1; return GS_OK; }
+    if (b->stage == 0) {
+        cudaError_t e = cudaEventQuery(b->ev_enq);
+        if (e == cudaErrorNotReady) return GS_OK;
+        if (e != cudaSuccess) return cuda_fail(e, "gs_eval_batch");
+        gs_status rc = collect_kernel(b);
+        if (rc != GS_OK) return rc;
+    }
+    for (size_t i = 0; i < b->active.size();) {
+        int d = 0;
+        gs_status rc = result_ready(b->sub[b->active[i]], &d);
+        if (rc != GS_OK) return rc;
+        if (!d) { ++i; continue; }
+        const uint32_t q = b->active[i];
+        b->active.erase(b->active.begin() + i);
+        rc = retire(b, q);
+        if (rc == GS_OK) rc = launch_todo(b);
+        if (rc != GS_OK) return rc;
+    }
+    if (!b->active.empty() || b->todo_next < b->todo.size()) return GS_OK;
+    gs_status rc = all_done(b);
+    if (rc != GS_OK) return rc;
+    *done = 1;
+    return GS_OK;
 }
 
 extern "C" {

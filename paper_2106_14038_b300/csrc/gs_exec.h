@@ -102,6 +102,17 @@ gs_status eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_stream, i
 gs_status eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n, void* cuda_stream,
                         const gs_batch_config* cfg, int max_blocks, gs_batch** out);
 uint64_t batch_device_bytes(const gs_batch* b);
+// Device bytes a batch of n queries will hold under cfg (slots + pool).
+uint64_t batch_estimate(const gs_graph* g, const gs_batch_config* cfg, uint32_t n,
+                        uint64_t pool_bytes);
+// Non-blocking progress of a batch: *done = 1 once every answer count is
+// known (the grid-path queries it handed on included).
+gs_status batch_advance(gs_batch* b, int* done);
+// Non-blocking: *done = 1 once a result's enqueued work has finished.
+gs_status result_ready(gs_result* r, int* done);
+// Waits for the result, then moves its answer rows into a right-sized
+// allocation and frees its workspace (fetches read the rows from there).
+gs_status result_compact(gs_result* r);
 
 uint64_t host_level_off(const uint64_t* n, int l);
 bool small_eligible(const gs_plan* P);

@@ -7,9 +7,11 @@
 //   - launch: the batch runs on its own stream (gs_eval_batch's persistent
 //     kernel), so batches admitted while others are running overlap on the
 //     device;
-//   - completion: in-flight batches are polled with events; a finished
-//     batch completes its tickets (answers stay on the device until the
-//     ticket is released) and returns its memory to the budget.
+//   - completion: in-flight batches advance without blocking (events): once
+//     the batch kernel is done, the queries it handed back are launched on
+//     the graph's side streams; once those are done too, the batch
+//     completes its tickets (answers stay on the device until the ticket
+//     is released) and returns its memory to the budget.
 // Callers submit and poll from their own threads; everything shared is
 // under one mutex, and CUDA work for one batch is only issued by the worker.
 #include <algorithm>
@@ -18,6 +20,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <new>
 #include <thread>
 #include <unordered_map>
@@ -38,6 +41,8 @@ struct Flight {
     std::vector<uint64_t> tickets;
     std::vector<const gs_plan*> plans;
     int refs = 0;                 // tickets not yet released
+    gs_status err = GS_OK;
+    std::string msg;
 };
 
 struct Ticket {
@@ -48,6 +53,7 @@ struct Ticket {
     uint32_t index = 0;
     uint64_t rows = 0;
     gs_status err = GS_OK;
+    std::string msg;              // why the query failed
 };
 
 }  // namespace
@@ -74,14 +80,14 @@ namespace {
 
 // Device bytes a batch of n queries will hold while it runs.
 uint64_t estimate(const gs_server* s, uint32_t n) {
-    const uint64_t slots = std::min<uint64_t>(n, (uint64_t)s->g->sm_count * batch_blocks_per_sm());
-    return slots * (24ull << 20) + (uint64_t)n * s->cfg.pool_bytes_per_query;
+    return batch_estimate(s->g, &s->cfg.batch, n, (uint64_t)n * s->cfg.pool_bytes_per_query);
 }
 
-void complete(gs_server* s, std::shared_ptr<Flight>& f) {
-    // called without the lock: may wait for queries handed to the grid path
+void complete(gs_server* s, std::shared_ptr<Flight>& f, gs_status rc) {
     std::vector<uint64_t> rows(f->tickets.size(), 0);
-    gs_status rc = gs_batch_info(f->b, rows.data(), nullptr);
+    if (rc == GS_OK) rc = gs_batch_info(f->b, rows.data(), nullptr);   // ready: no wait
+    std::string msg = f->msg;
+    if (rc != GS_OK && msg.empty()) msg = last_error();
     std::lock_guard<std::mutex> lk(s->mu);
     const auto now = Clock::now();
     for (size_t i = 0; i < f->tickets.size(); ++i) {
@@ -89,6 +95,7 @@ void complete(gs_server* s, std::shared_ptr<Flight>& f) {
         if (it == s->tickets.end()) continue;
         it->second.state = rc == GS_OK ? 2 : 3;
         it->second.err = rc;
+        it->second.msg = msg;
         it->second.rows = rows[i];
         it->second.done_at = now;
     }
@@ -105,19 +112,30 @@ void worker_loop(gs_server* s) {
             if (s->queue.empty() && s->inflight.empty())
                 s->cv.wait_for(lk, std::chrono::microseconds(s->cfg.max_wait_us));
             if (s->stopping && s->queue.empty() && s->inflight.empty()) break;
-            // completions
+            // completions (a batch's hand-backs run on the side streams; the
+            // worker only looks at events here and never waits)
             for (size_t i = 0; i < s->inflight.size();) {
                 int done = 0;
-                gs_batch_poll(s->inflight[i]->b, &done);
-                if (done) {
+                const gs_status rc = batch_advance(s->inflight[i]->b, &done);
+                if (rc != GS_OK || done) {
+                    s->inflight[i]->err = rc;
+                    if (rc != GS_OK) s->inflight[i]->msg = last_error();
+                    s->inflight_bytes -= s->inflight[i]->bytes;   // its workspaces are done
                     finished.push_back(s->inflight[i]);
                     s->inflight.erase(s->inflight.begin() + i);
                 } else {
                     ++i;
                 }
             }
-            // admission
-            while (!s->queue.empty()) {
+            // admission: a new batch starts when the device is idle, when
+            // max_batch / 8 queries wait, or when the oldest has waited
+            // max_wait_us; otherwise arrivals gather into the next batch
+            const bool ripe =
+                !s->queue.empty() &&
+                (s->inflight.empty() || s->queue.size() >= std::max<uint32_t>(1, s->cfg.max_batch / 8) ||
+                 Clock::now() - s->tickets[s->queue.front()].submitted >=
+                     std::chrono::microseconds(s->cfg.max_wait_us));
+            while (ripe && !s->queue.empty()) {
                 int st = -1;
                 for (size_t k = 0; k < s->streams.size(); ++k)
                     if (!s->stream_busy[k]) { st = (int)k; break; }
@@ -146,15 +164,17 @@ void worker_loop(gs_server* s) {
                     f->plans.push_back(t.plan);
                 }
                 f->refs = (int)take;
-                gs_batch_config bc{};
+                gs_batch_config bc = s->cfg.batch;
                 bc.pool_bytes = s->cfg.pool_bytes_per_query * take;
                 gs_status rc = eval_batch_ex(s->g, f->plans.data(), take, (void*)s->streams[st],
                                              &bc, 0, &f->b);
                 if (rc != GS_OK) {
+                    const std::string m = last_error();
                     for (uint64_t id : f->tickets) {
                         Ticket& t = s->tickets[id];
                         t.state = 3;
                         t.err = rc;
+                        t.msg = m;
                         t.done_at = Clock::now();
                     }
                     continue;
@@ -166,11 +186,7 @@ void worker_loop(gs_server* s) {
                 s->batches++;
             }
         }
-        for (auto& f : finished) {
-            complete(s, f);
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->inflight_bytes -= f->bytes;
-        }
+        for (auto& f : finished) complete(s, f, f->err);
         if (finished.empty()) {
             std::unique_lock<std::mutex> lk(s->mu);
             if (!s->inflight.empty() && s->queue.empty())
@@ -193,7 +209,7 @@ gs_status gs_server_start(gs_graph* g, const gs_server_config* cfg, gs_server** 
     c.max_batch = 1024;
     c.n_streams = 4;
     c.memory_budget = 40ull << 30;
-    c.max_wait_us = 50;
+    c.max_wait_us = 200;
     c.pool_bytes_per_query = 16ull << 20;
     if (cfg) {
         if (cfg->max_batch) c.max_batch = cfg->max_batch;
@@ -201,6 +217,8 @@ gs_status gs_server_start(gs_graph* g, const gs_server_config* cfg, gs_server** 
         if (cfg->memory_budget) c.memory_budget = cfg->memory_budget;
         if (cfg->max_wait_us) c.max_wait_us = cfg->max_wait_us;
         if (cfg->pool_bytes_per_query) c.pool_bytes_per_query = cfg->pool_bytes_per_query;
+        c.batch = cfg->batch;
+        c.batch.pool_bytes = 0;
     }
     s->cfg = c;
     for (uint32_t i = 0; i < c.n_streams; ++i) {
@@ -246,7 +264,11 @@ gs_status gs_server_poll(gs_server* s, uint64_t ticket, int* done, uint64_t* row
     auto it = s->tickets.find(ticket);
     if (it == s->tickets.end()) { set_error("gs_server_poll: unknown ticket %llu", (unsigned long long)ticket); return GS_EINVAL; }
     const Ticket& t = it->second;
-    if (t.state == 3) { set_error("gs_server_poll: the query failed"); *done = 1; return t.err; }
+    if (t.state == 3) {
+        set_error("gs_server_poll: the query failed: %s", t.msg.c_str());
+        *done = 1;
+        return t.err;
+    }
     *done = t.state == 2;
     if (*done) {
         if (rows) *rows = t.rows;
@@ -319,3 +341,47 @@ void gs_server_stop(gs_server* s) {
 }
 
 }  // extern "C"
+
+extern "C" gs_status gs_server_replay(gs_server* s, const gs_plan* const* plans, uint32_t n_plans,
+                                      const double* arrival_s, uint64_t n, double timeout_s,
+                                      double* latency_us, double* done_s) {
+    if (!s || (n && (!plans || !arrival_s || n_plans == 0))) {
+        set_error("gs_server_replay: NULL argument");
+        return GS_EINVAL;
+    }
+    const Clock::time_point t0 = Clock::now();
+    auto since = [&](Clock::time_point t) { return std::chrono::duration<double>(t - t0).count(); };
+    std::vector<uint64_t> ticket(n, 0);
+    uint64_t next = 0, head = 0;   // next to submit; oldest not yet seen done
+    std::vector<char> seen(n, 0);
+    gs_status fail = GS_OK;
+    while (head < n) {
+        const double now = since(Clock::now());
+        if (now > timeout_s) { set_error("gs_server_replay: not finished after %.1f s", timeout_s); return GS_ETIMEOUT; }
+        while (next < n && arrival_s[next] <= now) {
+            gs_status rc = gs_server_submit(s, plans[next % n_plans], &ticket[next]);
+            if (rc != GS_OK) return rc;
+            ++next;
+        }
+        // completions, oldest first; stop at the first still running
+        while (head < next) {
+            Clock::time_point done_at;
+            int state = 0;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                auto it = s->tickets.find(ticket[head]);
+                if (it == s->tickets.end()) { state = 3; }
+                else { state = it->second.state; done_at = it->second.done_at; if (state == 3) fail = it->second.err; }
+            }
+            if (state < 2) break;
+            if (latency_us) latency_us[head] = std::chrono::duration<double, std::micro>(done_at - t0).count() - arrival_s[head] * 1e6;
+            if (done_s) done_s[head] = since(done_at);
+            gs_server_release(s, ticket[head]);
+            ++head;
+        }
+        if (head < n && (next == n || arrival_s[next] > since(Clock::now()) + 20e-6))
+            std::this_thread::sleep_for(std::chrono::microseconds(10));
+    }
+    if (fail != GS_OK) { set_error("gs_server_replay: a query failed"); return fail; }
+    return GS_OK;
+}

@@ -429,3 +429,19 @@ def test_server_answers_equal_alone(rmat14):
     assert done == len(order) and batches >= 2
     assert peak <= budget
     srv.stop()
+
+
+def test_server_replay_completes_every_arrival(rmat14):
+    # native Poisson replay: every query finishes, latencies are positive and
+    # completions come after arrivals
+    w, (s, p, o), g, ix = rmat14
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    plans = [g.plan(q.patterns) for q in rdfgen.queries(w, sm)]
+    rng = np.random.default_rng(11)
+    sched = np.cumsum(rng.exponential(1.0 / 5000.0, 300))
+    srv = gs.Server(g, max_batch=64)
+    lat, done = srv.replay(plans, sched, timeout_s=60)
+    completed, batches, _ = srv.stats()
+    srv.stop()
+    assert completed == 300 and batches >= 1
+    assert (lat > 0).all() and (done >= sched).all()
