@@ -445,3 +445,31 @@ def test_server_replay_completes_every_arrival(rmat14):
     srv.stop()
     assert completed == 300 and batches >= 1
     assert (lat > 0).all() and (done >= sched).all()
+
+
+@pytest.mark.slow
+def test_scan_full_size_rmat26():
+    # the bandwidth workload's graph (scale 26, 2^30 draws, 1.07e9 distinct
+    # triples, 256 predicates): every word of two grouped scans equals the
+    # AND of presence vectors computed on the host from the raw triples
+    w = rdfgen.WORKLOADS["rmat26"]
+    s, p, o = rdfgen.graph(w)
+    g = gs.Graph(s, p, o, w.n_vertices, w.n_preds)
+    N = w.n_vertices
+    pres = {}
+
+    def presence(d, q):
+        if (d, q) not in pres:
+            f = np.zeros(N, bool)
+            f[(o if d else s)[p == q]] = True
+            pres[(d, q)] = f
+        return pres[(d, q)]
+
+    for preds, dirs in [([1, 2, 3, 1, 2], [0, 0, 0, 1, 1]), ([4, 200, 7], [1, 0, 1])]:
+        want = np.ones(N, bool)
+        for q, d in zip(preds, dirs):
+            want &= presence(d, q)
+        got = g.scan(preds, dirs).cpu().numpy().view(np.uint32)
+        want_words = np.packbits(want, bitorder="little").view(np.uint32)
+        assert np.array_equal(got, want_words), (preds, dirs)
+    g.close()
