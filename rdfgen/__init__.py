@@ -59,6 +59,8 @@ def _L():
         lib.rdfgen_embed.argtypes = [vp, u32, u32, vp, vp, vp, u64, u64, vp, vp, vp]
         lib.rdfgen_tree_bound.restype = dbl
         lib.rdfgen_tree_bound.argtypes = [vp, u32, vp, vp, vp, vp, vp]
+        lib.rdfgen_tree_bound_rooted.restype = dbl
+        lib.rdfgen_tree_bound_rooted.argtypes = [vp, u32, vp, vp, vp, vp, vp, u32, u64]
         _lib = lib
     return _lib
 
@@ -159,7 +161,12 @@ class Sampler:
         except Exception:
             pass
 
-    def embed(self, shape: Shape, seed: int, attempt: int, with_bound: bool = True):
+    def embed(self, shape: Shape, seed: int, attempt: int, with_bound: bool = True,
+              work_cap: int = 0):
+        """One seeded embedding of shape (None if the walk fails). With
+        work_cap > 0 and a constant in the shape, the bound is counted from
+        the first constant through the vertices actually reached, and is inf
+        when that visits more than work_cap adjacency entries."""
         se = np.array(shape.edges, np.uint32).reshape(-1)
         isc = np.zeros(shape.n_v, np.uint8)
         isc[list(shape.const)] = 1
@@ -174,13 +181,19 @@ class Sampler:
         if rc != 0:
             return None
         bound = float("nan")
-        if with_bound:
+        if with_bound and work_cap > 0 and shape.const:
+            bound = _L().rdfgen_tree_bound_rooted(self._h, shape.n_v, _ptr(se), _ptr(isc),
+                                                  _ptr(mapped), _ptr(pat), _ptr(usub),
+                                                  int(shape.const[0]), int(work_cap))
+            if bound < 0:
+                bound = float("inf")
+        elif with_bound:
             bound = _L().rdfgen_tree_bound(self._h, shape.n_v, _ptr(se), _ptr(isc), _ptr(mapped),
                                            _ptr(pat), _ptr(usub))
         return Query(pat, shape.n_v - len(shape.const), shape.name, bound, mapped)
 
     def sample(self, shape: Shape, seed: int, qid: int, cap: float, tries: int = 3,
-               escalate: bool = True):
+               escalate: bool = True, work_cap: int = 0):
         """First embedding of `shape` whose spanning-tree bound is <= cap.
 
         After `tries` rejected attempts one more shape vertex (drawn from the
@@ -191,7 +204,7 @@ class Sampler:
         while True:
             rejected, raw = 0, 0
             while rejected < tries and raw < 64 * tries:
-                q = self.embed(sh, seed, qid * 100003 + a)
+                q = self.embed(sh, seed, qid * 100003 + a, work_cap=work_cap)
                 a += 1
                 raw += 1
                 if q is None:
@@ -278,6 +291,63 @@ def _shapes_mixed(w: Workload):
         sh.const = sorted(picks)
         out.append(sh)
     return out
+
+
+def _shapes_batched(w: Workload, n: int):
+    """2..10 shape vertices, shape classes uniform, 1..2 constants (so the
+    bound can be counted from a constant), and a target match count t drawn
+    log-uniformly from [1, 10^6]; returns (shape, t) pairs."""
+    out = []
+    for q in range(n):
+        r = draw(w.query_seed, 30, q)
+        kind = r % 4
+        n_v = 2 + (r >> 4) % 9                      # 2..10
+        if kind == 0 or n_v == 2:
+            sh = star(n_v - 1)
+        elif kind == 1:
+            sh = chain(n_v - 1)
+        elif kind == 2:
+            sh = cycle(n_v)
+        else:
+            n_v = max(n_v, 4)
+            rest = n_v - 3
+            a = (r >> 12) % (rest + 1)
+            sh = snowflake([a, rest - a])
+        n_const = 1 + (r >> 20) % 2
+        n_const = min(n_const, sh.n_v - 1)
+        verts = list(range(sh.n_v))
+        picks = []
+        for j in range(n_const):
+            idx = draw(w.query_seed, 31, q * 8 + j) % len(verts)
+            picks.append(verts.pop(idx))
+        sh.const = sorted(picks)
+        t = 10.0 ** (6.0 * (draw(w.query_seed, 32, q) % 1000003) / 1000003.0)
+        out.append((sh, t))
+    return out
+
+
+def batched_queries(w: Workload, sampler: Sampler, n: int | None = None,
+                    work_cap: int = 5_000_000, threads: int | None = None):
+    """The batched workload's queries: each shape's first embedding whose
+    spanning-tree bound (counted from its first constant) is at most its
+    target; more constants after three rejections, and a ten times larger
+    target when every vertex but one is constant."""
+    import concurrent.futures as cf
+    import os
+    pairs = _shapes_batched(w, w.n_queries if n is None else n)
+
+    def one(q):   # a pure function of (seed, q): thread order does not matter
+        sh, cap = pairs[q]
+        while True:   # no embedding within the target: the next larger decade
+            try:
+                return sampler.sample(sh, w.query_seed, q, cap, work_cap=work_cap)
+            except RuntimeError:
+                if cap > 1e7:
+                    raise
+                cap *= 10.0
+
+    with cf.ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
+        return list(ex.map(one, range(len(pairs))))
 
 
 def queries(w: Workload, sampler: Sampler, n: int | None = None):

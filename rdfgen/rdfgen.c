@@ -426,3 +426,93 @@ double rdfgen_tree_bound(const rdf_adj* g, uint32_t n_sv, const uint32_t* se,
     free(f); free(tmp); free(pe); free(order);
     return total;
 }
+
+/* Tree bound rooted at a constant: the same spanning-tree match count as
+ * rdfgen_tree_bound, computed top-down from shape vertex `root` (which must
+ * be a constant) through the adjacency of the vertices actually reached,
+ * with memoisation per (shape vertex, graph vertex). Returns -1 once more
+ * than work_cap adjacency entries have been visited (the query is then far
+ * too unselective to keep). Input selection only. */
+typedef struct { uint32_t* key; double* val; uint64_t cap, n; } memo_t;
+
+static double* memo_get(memo_t* m, uint32_t k, int* fresh) {
+    if (2 * (m->n + 1) > m->cap) {
+        uint64_t nc = m->cap ? 2 * m->cap : 1024;
+        uint32_t* nk = (uint32_t*)malloc(sizeof(uint32_t) * nc);
+        double* nv = (double*)malloc(sizeof(double) * nc);
+        for (uint64_t i = 0; i < nc; ++i) nk[i] = 0xffffffffu;
+        for (uint64_t i = 0; i < m->cap; ++i) {
+            if (m->key[i] == 0xffffffffu) continue;
+            uint64_t h = mix64(m->key[i]) & (nc - 1);
+            while (nk[h] != 0xffffffffu) h = (h + 1) & (nc - 1);
+            nk[h] = m->key[i]; nv[h] = m->val[i];
+        }
+        free(m->key); free(m->val);
+        m->key = nk; m->val = nv; m->cap = nc;
+    }
+    uint64_t h = mix64(k) & (m->cap - 1);
+    while (m->key[h] != 0xffffffffu) {
+        if (m->key[h] == k) { *fresh = 0; return &m->val[h]; }
+        h = (h + 1) & (m->cap - 1);
+    }
+    m->key[h] = k; m->n++; *fresh = 1;
+    return &m->val[h];
+}
+
+typedef struct {
+    const rdf_adj* g;
+    uint32_t n_sv;
+    const uint32_t* se;
+    const uint8_t* is_const;
+    const uint32_t* mapped;
+    const int64_t* patterns;
+    const uint8_t* u_subject;
+    memo_t* memo;
+    uint64_t work, cap;
+} rooted_t;
+
+/* matches of the subtree of shape vertex w (away from tree edge via) with w -> y */
+static double rooted_count(rooted_t* c, uint32_t w, uint32_t y, int64_t via) {
+    if (c->is_const[w] && c->mapped[w] != y) return 0.0;
+    int fresh = 0;
+    double* slot = memo_get(&c->memo[w], y, &fresh);
+    if (!fresh) return *slot;
+    *slot = 0.0;
+    double prod = 1.0;
+    for (uint32_t e = 0; e + 1 < c->n_sv && prod != 0.0; ++e) {
+        if ((int64_t)e == via) continue;
+        uint32_t a = c->se[2 * e], b = c->se[2 * e + 1], u;
+        int w_subj;
+        if (a == w) { u = b; w_subj = c->u_subject[e] != 0; }
+        else if (b == w) { u = a; w_subj = c->u_subject[e] == 0; }
+        else continue;
+        const uint32_t p = (uint32_t)c->patterns[3 * e + 1];
+        const uint64_t* off = w_subj ? c->g->out_off : c->g->in_off;
+        const uint64_t* ix = w_subj ? c->g->out_idx : c->g->in_idx;
+        double sum = 0.0;
+        for (uint64_t t = off[y]; t < off[y + 1]; ++t) {
+            if (++c->work > c->cap) return 0.0;
+            const uint64_t ti = ix[t];
+            if (c->g->p[ti] != p) continue;
+            sum += rooted_count(c, u, w_subj ? c->g->o[ti] : c->g->s[ti], (int64_t)e);
+            if (c->work > c->cap) return 0.0;
+        }
+        prod *= sum;
+    }
+    slot = memo_get(&c->memo[w], y, &fresh);   /* the table may have moved */
+    *slot = prod;
+    return prod;
+}
+
+double rdfgen_tree_bound_rooted(const rdf_adj* g, uint32_t n_sv, const uint32_t* se,
+                                const uint8_t* is_const, const uint32_t* mapped,
+                                const int64_t* patterns, const uint8_t* u_subject, uint32_t root,
+                                uint64_t work_cap) {
+    if (root >= n_sv || !is_const[root]) return -1.0;
+    rooted_t c = {g, n_sv, se, is_const, mapped, patterns, u_subject, NULL, 0, work_cap};
+    c.memo = (memo_t*)calloc(n_sv, sizeof(memo_t));
+    double total = rooted_count(&c, root, mapped[root], -1);
+    for (uint32_t v = 0; v < n_sv; ++v) { free(c.memo[v].key); free(c.memo[v].val); }
+    free(c.memo);
+    return c.work > work_cap ? -1.0 : total;
+}

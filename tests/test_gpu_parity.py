@@ -473,3 +473,30 @@ def test_scan_full_size_rmat26():
         want_words = np.packbits(want, bitorder="little").view(np.uint32)
         assert np.array_equal(got, want_words), (preds, dirs)
     g.close()
+
+
+@pytest.mark.slow
+def test_batched_workload_rmat24_sample_equals_oracle():
+    # the batched workload's graph (scale 24, 2^28 draws, 128 predicates) and
+    # 96 of its queries in one batch under the autotuned configuration: every
+    # answer equals the oracle's sorted rows
+    import time
+    w = rdfgen.WORKLOADS["rmat24"]
+    s, p, o = rdfgen.graph(w)
+    g = gs.Graph(s, p, o, w.n_vertices, w.n_preds)
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    qs = rdfgen.batched_queries(w, sm, 96)
+    sm.close()
+    pats = [q.patterns for q in qs]
+    cfg, _ = g.autotune_batch(pats[:32])
+    b = g.eval_batch(pats, config=cfg)
+    rows = b.rows()
+    t0 = time.time()
+    ix = oracle.Index(s, p, o, w.n_vertices, w.n_preds)
+    print("oracle index %.1f s" % (time.time() - t0))
+    for i, pt in enumerate(pats):
+        want = ix.eval(pt, threads=os.cpu_count() or 1)
+        assert int(rows[i]) == len(want), i
+        assert np.array_equal(b.fetch(i), want), i
+    b.close()
+    g.close()
