@@ -107,3 +107,23 @@ def test_planner_examples_6_1_and_6_2():
 def test_planner_rejects_bad_queries(pat):
     rc, _ = _plan_nograph(pat)
     assert rc == 1  # GS_EINVAL
+
+
+def test_null_arguments_are_a_status_not_a_crash():
+    # host-side argument checks of the batch, tuning, serving and scan calls
+    lib = gs.load_library()
+    vp = ctypes.c_void_p
+    h = ctypes.c_void_p()
+    cfg = gs.BatchConfig()
+    ms = ctypes.c_float()
+    assert lib.gs_eval_batch(None, None, 1, None, ctypes.byref(h)) == 1
+    assert lib.gs_eval_batch_cfg(None, None, 1, ctypes.byref(cfg), None, ctypes.byref(h)) == 1
+    assert lib.gs_batch_autotune(None, None, 1, None, ctypes.byref(cfg), ctypes.byref(ms)) == 1
+    assert lib.gs_server_start(None, None, ctypes.byref(h)) == 1
+    assert lib.gs_server_replay(None, None, 0, None, 0, 1.0, None, None) == 1
+    assert lib.gs_scan_candidates(None, None, None, 0, None, None) == 1
+    assert lib.gs_scan_candidates_noalloc(None, None, None, 0, None, None) == 1
+    assert lib.gs_batch_info(None, None, None) == 1
+    assert lib.gs_server_poll(None, 1, None, None, None) == 1
+    assert lib.gs_last_error()
+    assert lib.gs_noalloc_scratch_bytes() == 48 << 20

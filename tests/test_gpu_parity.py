@@ -166,6 +166,25 @@ def test_scan_rows_crossing_work_items(shape):
         assert np.array_equal(got, want), (shape, preds, dirs)
 
 
+@pytest.mark.parametrize("n_p", [3000, 60000])
+def test_scan_many_predicates(n_p):
+    # large predicate ids: the one-hot table no longer fits beside the full
+    # warp count (16-bit table with fewer warps, or the byte table)
+    rng = np.random.default_rng(n_p)
+    n_v = 5000
+    s = rng.integers(0, n_v, 60000)
+    o = rng.integers(0, n_v, 60000)
+    p = rng.integers(1, n_p + 1, 60000)
+    p[:20000] = rng.integers(n_p - 5, n_p + 1, 20000)     # frequent high ids
+    g, ix = _graph(s, p, o, n_v, n_p)
+    for preds, dirs in [([n_p, n_p - 1], [0, 1]), ([1, n_p - 3, n_p - 4], [1, 0, 0])]:
+        want = np.ones(n_v, bool)
+        for q, d in zip(preds, dirs):
+            want &= ix.presence(int(d), int(q)).astype(bool)
+        got = _bits_to_bool(g.scan(preds, dirs), n_v)
+        assert np.array_equal(got, want), (n_p, preds, dirs)
+
+
 def _same(g, ix, pats, flags=0):
     got = g.query(pats, sort=True, flags=flags)
     want = ix.eval(pats, threads=4)
