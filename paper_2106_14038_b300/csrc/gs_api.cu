@@ -82,6 +82,7 @@ namespace {
 constexpr uint64_t kArenaMin = 64ull << 20;
 constexpr uint64_t kArenaDefault = 512ull << 20;
 constexpr uint64_t kArenaSmall = 64ull << 20;   // enough for the single-block budgets
+constexpr uint64_t kSmallRoute = 8192;          // first-level bound above which a query goes straight to the grid path
 constexpr int kMaxRetries = 16;
 
 ExecDev exec_view(gs_result* r) {
@@ -220,6 +221,19 @@ gs_status gs_load_triples(const uint32_t* s, const uint32_t* p, const uint32_t* 
     set_pool_threshold(dev);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     gs_status rc = build_store(g, s, p, o, n, inputs_on_device != 0, st);
+    if (rc == GS_OK) {
+        // row lengths on the host (routing estimates)
+        std::vector<uint32_t> ptr((size_t)g->N + 1);
+        for (int d = 0; d < 2 && rc == GS_OK; ++d) {
+            const Store& S = d ? g->in : g->out;
+            cudaError_t e = cudaMemcpy(ptr.data(), S.ptr, sizeof(uint32_t) * ptr.size(),
+                                       cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "gs_load_triples"); break; }
+            std::vector<uint32_t>& deg = d ? g->deg_in : g->deg_out;
+            deg.resize(g->N);
+            for (uint32_t v = 0; v < g->N; ++v) deg[v] = ptr[v + 1] - ptr[v];
+        }
+    }
     if (rc != GS_OK) {
         free_store(g, st);
         cudaStreamSynchronize(st);
@@ -229,6 +243,8 @@ gs_status gs_load_triples(const uint32_t* s, const uint32_t* p, const uint32_t* 
     *out = g;
     return GS_OK;
 }
+
+
 
 gs_status gs_graph_info(const gs_graph* g, uint64_t* n_triples, uint32_t* n_vertices,
                         uint32_t* n_predicates) {
@@ -278,6 +294,21 @@ gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint
 }
 
 }  // extern "C"
+
+// An upper bound on the candidates of the plan's first level when it is
+// seeded from constants (their row or column lengths), else UINT64_MAX.
+uint64_t gs::first_level_bound(const gs_graph* g, const gs_plan* plan) {
+    if (plan->n_levels == 0 || g->deg_out.empty()) return ~0ull;
+    const LevelSpec& L = plan->levels[0];
+    if (L.src != kSrcBinders) return ~0ull;
+    uint64_t best = ~0ull;
+    for (int b = 0; b < L.n_binders; ++b) {
+        const Binder& B = L.b[b];
+        if (!B.from_const || B.c >= g->N) continue;
+        best = std::min<uint64_t>(best, B.dir == 0 ? g->deg_out[B.c] : g->deg_in[B.c]);
+    }
+    return best;
+}
 
 gs_status gs::result_compact(gs_result* r) {
     gs_status rc = wait_result(r);
@@ -349,7 +380,9 @@ gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_strea
         r->lists = (uint32_t*)g->alloc.get(4ull * g->N * plan->n_levels, r->st);
         if (!r->lists) { set_error("gs_eval_query: out of device memory"); rc = GS_ENOMEM; }
     }
-    r->mode = (small_eligible(plan) && !force_grid) ? 1 : 0;
+    // the single-CTA evaluator unless the first level is certainly past its
+    // budget (then it would only hand the query back)
+    r->mode = (small_eligible(plan) && !force_grid && first_level_bound(g, plan) <= kSmallRoute) ? 1 : 0;
     if (rc == GS_OK) {
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);

@@ -241,7 +241,8 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
     uint32_t n_in = 0;
     for (uint32_t q = 0; q < n; ++q) {
         b->n_vars[q] = plans[q]->n_vars;
-        if (rec_fits(plans[q])) {
+        // a first level certainly past the candidate budget goes to the grid path
+        if (rec_fits(plans[q]) && first_level_bound(g, plans[q]) <= 8 * b->cfg.cand_budget) {
             b->in_kernel[q] = 1;
             off[n_in] = total;
             b->kidx.push_back(q);

@@ -246,11 +246,20 @@ __global__ void __launch_bounds__(kThreads) k_enum_range(ExecDev E, int last, En
     if (threadIdx.x == 0) ctl->bsum[blockIdx.x] = sum;
 }
 
+// Tiles of answer rows: consecutive threads take consecutive rows (their
+// node data and leaf entries are then shared or adjacent), decode the leaf
+// digits (32-bit division when the offset fits), and stage the rows in
+// shared memory; the tile is written out with 16-byte stores.
+constexpr uint32_t kEnumStageWords = 7168;    // 28 KB of staged rows
+constexpr uint32_t kEnumTileNodes = 2048;     // row offsets of a tile's nodes kept in shared memory
+
 __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, EnumSpec F) {
     Ctl* ctl = E.ctl;
     if (overflowed(ctl) || (ctl->status & kStHuge)) return;
     __shared__ const uint2* lv[kMaxLevels];
     __shared__ uint64_t tile_nodes[2];
+    __shared__ __align__(16) uint32_t stage[kEnumStageWords];
+    __shared__ uint64_t roff_s[kEnumTileNodes + 1];
     load_levels(E, last, lv);
     const uint64_t n = ctl->n[last];
     const uint32_t nl = F.n_leaves > 0 ? F.n_leaves : 1;
@@ -258,41 +267,79 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
     const uint64_t T = ctl->rows;
     uint64_t out_off = kCtlBytes;
     for (int j = 0; j <= last; ++j) out_off += align256(8ull * ctl->n[j]);
-    const uint64_t rowb = 4ull * F.n_vars;
+    const uint32_t nv = (uint32_t)F.n_vars;
+    const uint64_t rowb = 4ull * nv;
     const uint64_t cap = S.base > out_off ? (S.base - out_off) / rowb : 0;
     if (T > cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->status, kStOverflow);
         return;
     }
-    int32_t* out = (int32_t*)(E.arena + out_off);
-    for (uint64_t t0 = (uint64_t)blockIdx.x * kExpTile; t0 < T; t0 += (uint64_t)gridDim.x * kExpTile) {
-        uint64_t t1 = min(t0 + kExpTile, T);
+    uint8_t* out = E.arena + out_off;   // 256-byte aligned
+    // rows per tile: a multiple of 4 (so every tile starts on 16 bytes)
+    const uint32_t tile_rows = min(kThreads * 8u, (kEnumStageWords / nv) & ~3u);
+    for (uint64_t t0 = (uint64_t)blockIdx.x * tile_rows; t0 < T; t0 += (uint64_t)gridDim.x * tile_rows) {
+        const uint64_t t1 = min(t0 + tile_rows, T);
         if (threadIdx.x == 0) {
             tile_nodes[0] = upper_bound_u64(S.roff, 0, n, t0) - 1;
             tile_nodes[1] = upper_bound_u64(S.roff, tile_nodes[0], n, t1 - 1);
         }
         __syncthreads();
         const uint64_t i0 = tile_nodes[0], i1 = tile_nodes[1];
-        for (int k = 0; k < kExpItems; ++k) {
-            uint64_t q = t0 + (uint64_t)k * kThreads + threadIdx.x;
-            if (q >= t1) continue;
-            uint64_t i = upper_bound_u64(S.roff, i0, i1, q) - 1;
-            uint64_t loc = q - S.roff[i];
-            uint32_t vid[kMaxLevels];
-            walk(lv, last, (uint32_t)i, vid);
-            uint32_t leafv[kMaxVars];
-            for (int j = F.n_leaves - 1; j >= 0; --j) {
-                uint2 r = S.rng[i * nl + j];
-                uint64_t d = loc % r.y;
-                loc /= r.y;
-                leafv[j] = __ldg(store_of(E, F.leaf[j].dir).idx + r.x + d);
+        // the tile's node offsets in shared memory (when they fit): the row ->
+        // node search then runs there
+        const bool local = i1 - i0 <= kEnumTileNodes;
+        if (local)
+            for (uint64_t k = threadIdx.x; k < i1 - i0; k += kThreads) roff_s[k] = S.roff[i0 + k];
+        __syncthreads();
+        for (uint64_t q = t0 + threadIdx.x; q < t1; q += kThreads) {
+            uint64_t i, base;
+            if (local) {
+                uint32_t lo = 0, hi = (uint32_t)(i1 - i0);   // last k with roff_s[k] <= q
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (roff_s[mid] <= q) lo = mid; else hi = mid;
+                }
+                i = i0 + lo;
+                base = roff_s[lo];
+            } else {
+                i = upper_bound_u64(S.roff, i0, i1, q) - 1;
+                base = S.roff[i];
             }
-            int32_t* row = out + q * F.n_vars;
-            for (int v = 0; v < F.n_vars; ++v) {
-                int32_t src = F.var_src[v];
-                row[v] = (int32_t)(src >= 0 ? vid[src] : leafv[-src - 1]);
+            uint64_t loc = q - base;
+            // straight into the staged row: each level's and leaf's column
+            uint32_t* row = stage + (q - t0) * nv;
+            uint32_t node = (uint32_t)i;
+            for (int j = last; j >= 0; --j) {
+                const uint2 e = lv[j][node];
+                row[F.col_of_level[j]] = e.x;
+                node = e.y;
+            }
+            if (loc < (1ull << 32)) {
+                uint32_t l32 = (uint32_t)loc;
+                for (int j = F.n_leaves - 1; j >= 0; --j) {
+                    const uint2 r = S.rng[i * nl + j];
+                    const uint32_t d = l32 % r.y;
+                    l32 /= r.y;
+                    row[F.col_of_leaf[j]] = __ldg(store_of(E, F.leaf[j].dir).idx + r.x + d);
+                }
+            } else {
+                for (int j = F.n_leaves - 1; j >= 0; --j) {
+                    const uint2 r = S.rng[i * nl + j];
+                    const uint64_t d = loc % r.y;
+                    loc /= r.y;
+                    row[F.col_of_leaf[j]] = __ldg(store_of(E, F.leaf[j].dir).idx + r.x + d);
+                }
             }
         }
+        __syncthreads();
+        // the tile's rows are contiguous in the output: 16-byte stores, then the tail
+        const uint64_t bytes = (t1 - t0) * rowb;
+        uint8_t* dst = out + t0 * rowb;
+        const uint64_t n16 = bytes / 16;
+        for (uint64_t k = threadIdx.x; k < n16; k += kThreads)
+            reinterpret_cast<uint4*>(dst)[k] = reinterpret_cast<const uint4*>(stage)[k];
+        for (uint64_t k = n16 * 4 + threadIdx.x; k < bytes / 4; k += kThreads)
+            reinterpret_cast<uint32_t*>(dst)[k] = stage[k];
         __syncthreads();
     }
 }
@@ -348,6 +395,8 @@ gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, vo
     F.n_vars = P->n_vars;
     for (int j = 0; j < P->n_leaves; ++j) F.leaf[j] = P->leaves[j];
     for (int v = 0; v < P->n_vars; ++v) F.var_src[v] = P->var_src[v];
+    for (int l = 0; l < P->n_levels; ++l) F.col_of_level[l] = P->levels[l].var;
+    for (int j = 0; j < P->n_leaves; ++j) F.col_of_leaf[j] = P->leaves[j].var;
     const uint32_t nl = P->n_leaves > 0 ? P->n_leaves : 1;
     k_enum_range<<<nb, kThreads, 0, st>>>(E, last, F);
     k_scan_block_sums<<<1, kThreads, 0, st>>>(ctl->bsum, ctl->boff, nb, &ctl->rows, &ctl->status);

@@ -45,6 +45,8 @@ struct EnumSpec {
     int32_t n_vars;
     LeafSpec leaf[kMaxVars];
     int32_t var_src[kMaxVars];
+    int32_t col_of_level[kMaxLevels];   // answer column of each level's variable
+    int32_t col_of_leaf[kMaxVars];      // answer column of each leaf
 };
 
 // The whole schedule of one query, passed by value to single-block kernels.
@@ -116,6 +118,9 @@ gs_status result_compact(gs_result* r);
 
 uint64_t host_level_off(const uint64_t* n, int l);
 bool small_eligible(const gs_plan* P);
+// An upper bound on the plan's first-level candidates from its constants'
+// row / column lengths (UINT64_MAX without a constant seed).
+uint64_t first_level_bound(const gs_graph* g, const gs_plan* plan);
 gs_status enqueue_small(const gs_plan* P, const ExecDev& E, uint32_t* launches, cudaStream_t st);
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
                        cudaStream_t st);

@@ -95,6 +95,10 @@ struct gs_graph {
     // side by side (created on first use, destroyed with the graph)
     cudaStream_t side[16] = {};
     int n_side = 0;
+    // host copies of the row lengths (out = CSR, in = CSC), used to route
+    // queries whose first level is certainly large away from the
+    // single-CTA evaluator
+    std::vector<uint32_t> deg_out, deg_in;
 };
 
 namespace gs {
