@@ -88,6 +88,10 @@ class Clocks:
 
     def __exit__(self, *a):
         if self.proc:
+            # a short timed region may end before nvidia-smi's first line
+            t0 = time.time()
+            while len(self.lines) < 1 and time.time() - t0 < 2.0:
+                time.sleep(0.02)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
