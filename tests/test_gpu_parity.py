@@ -519,3 +519,25 @@ def test_batched_workload_rmat24_sample_equals_oracle():
         assert np.array_equal(b.fetch(i), want), i
     b.close()
     g.close()
+
+
+@pytest.mark.slow
+def test_plain_and_batched_rmat22_workload_equal_oracle():
+    # the bench's workload at full size (scale 22, 66.9M triples, its 32
+    # queries, 20.4M answer rows): one at a time and as one autotuned batch,
+    # every row equal to the oracle's sorted rows
+    w = rdfgen.WORKLOADS["rmat22"]
+    s, p, o = rdfgen.graph(w)
+    g = gs.Graph(s, p, o, w.n_vertices, w.n_preds)
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    pats = [q.patterns for q in rdfgen.queries(w, sm)]
+    sm.close()
+    ix = oracle.Index(s, p, o, w.n_vertices, w.n_preds)
+    cfg, _ = g.autotune_batch(pats)
+    b = g.eval_batch(pats, config=cfg)
+    for i, pt in enumerate(pats):
+        want = ix.eval(pt, threads=os.cpu_count() or 1)
+        assert np.array_equal(g.query(pt), want), i
+        assert np.array_equal(b.fetch(i), want), i
+    b.close()
+    g.close()
