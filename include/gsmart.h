@@ -51,9 +51,11 @@ typedef enum {
     GS_ENOTIMPL = 6    /* feature not available in this build */
 } gs_status;
 
-/* Device allocation hook. alloc returns NULL on failure; both run on the
- * host thread that made the library call, with the stream the memory is
- * used on. */
+/* Device allocation hook. alloc returns NULL on failure, else memory
+ * aligned to 256 bytes as cudaMalloc's is (a less aligned block is handed
+ * back to free and the call fails as out of memory); both run on the host
+ * thread that made the library call, with the stream the memory is used
+ * on. */
 typedef struct {
     void* (*alloc)(size_t bytes, void* cuda_stream, void* ctx);
     void (*free)(void* ptr, void* cuda_stream, void* ctx);

@@ -298,13 +298,23 @@ class Graph:
 class Plan:
     def __init__(self, graph: Graph, patterns, flags: int = PLAN_DEGREE):
         load_library()
-        pat = np.ascontiguousarray(np.asarray(patterns, dtype=np.int64).reshape(-1, 3))
+        pat = patterns
+        if not (isinstance(pat, np.ndarray) and pat.dtype == np.int64 and pat.ndim == 2
+                and pat.flags.c_contiguous):
+            pat = np.ascontiguousarray(np.asarray(patterns, dtype=np.int64).reshape(-1, 3))
         h = ctypes.c_void_p()
-        _check(_lib.gs_plan_query(graph._h, pat.ctypes.data_as(ctypes.c_void_p), len(pat),
-                                  flags, ctypes.byref(h)))
+        _check(_lib.gs_plan_query(graph._h, pat.ctypes.data, len(pat), flags, ctypes.byref(h)))
         self._h = h
         self.patterns = pat
-        self.n_vars = int(-pat[:, [0, 2]][pat[:, [0, 2]] < 0].min()) if (pat[:, [0, 2]] < 0).any() else 0
+        self._n_vars = None
+
+    @property
+    def n_vars(self) -> int:
+        """Number of variables (answer columns)."""
+        if self._n_vars is None:
+            ends = self.patterns[:, [0, 2]]
+            self._n_vars = int(-ends[ends < 0].min()) if (ends < 0).any() else 0
+        return self._n_vars
 
     def describe(self):
         """(groups, roots): groups = [(vertex, [edge indices])]; a vertex is a

@@ -1,6 +1,7 @@
 // The C ABI (include/gsmart.h): argument checks, object lifetimes, the
 // workspace retry loop and the device row sort used by gs_fetch_bindings.
 #include <algorithm>
+#include <chrono>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -69,7 +70,9 @@ struct gs_result {
     void* work = nullptr;
     uint32_t* lists = nullptr;
     uint64_t list_stride = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the kernels
+    cudaEvent_t ev2 = nullptr;                 // the head copy has landed
+    uint8_t* head = nullptr;  // pinned copy of the control block's head
     bool ready = false;
     int mode = 0;             // 0: grid path, 1: single-block kernel
     uint32_t launches = 0;
@@ -78,6 +81,49 @@ struct gs_result {
 };
 
 namespace {
+
+constexpr uint64_t kHeadSlot = (kCtlHead + 127) & ~127ull;
+constexpr uint32_t kHeadSlotsPerBlock = 256;
+
+// The events and the pinned head slot of a result, from the graph's pools.
+gs_status take_host_res(gs_graph* g, cudaEvent_t* ev[3], uint8_t** head) {
+    std::lock_guard<std::mutex> lk(g->res_mu);
+    for (int i = 0; i < 3; ++i) {
+        cudaEvent_t* e = ev[i];
+        if (!g->ev_free.empty()) { *e = g->ev_free.back(); g->ev_free.pop_back(); }
+        else GS_CUDA(cudaEventCreate(e));
+    }
+    if (g->head_free.empty()) {
+        uint8_t* blk = nullptr;
+        GS_CUDA(cudaMallocHost(&blk, kHeadSlot * kHeadSlotsPerBlock));
+        g->head_blocks.push_back(blk);
+        for (uint32_t i = 0; i < kHeadSlotsPerBlock; ++i) g->head_free.push_back(blk + i * kHeadSlot);
+    }
+    *head = g->head_free.back();
+    g->head_free.pop_back();
+    return GS_OK;
+}
+
+// Free device memory as last seen, looked up again when older than 0.2 s
+// (the query needs only its order of magnitude).
+uint64_t free_device_bytes(gs_graph* g) {
+    std::lock_guard<std::mutex> lk(g->res_mu);
+    const auto now = std::chrono::steady_clock::now();
+    if (g->free_seen == 0 || now - g->free_seen_at > std::chrono::milliseconds(200)) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) cudaGetLastError();
+        g->free_seen = free_b;
+        g->free_seen_at = now;
+    }
+    return g->free_seen;
+}
+
+void give_host_res(gs_graph* g, const cudaEvent_t ev[3], uint8_t* head) {
+    std::lock_guard<std::mutex> lk(g->res_mu);
+    for (int i = 0; i < 3; ++i)
+        if (ev[i]) g->ev_free.push_back(ev[i]);
+    if (head) g->head_free.push_back(head);
+}
 
 constexpr uint64_t kArenaMin = 64ull << 20;
 constexpr uint64_t kArenaDefault = 512ull << 20;
@@ -106,6 +152,9 @@ gs_status enqueue(gs_result* r) {
         : enqueue_eval(r->g, &r->plan, exec_view(r), r->work, &r->launches, r->st);
     if (rc != GS_OK) return rc;
     GS_CUDA(cudaEventRecord(r->ev1, r->st));
+    // the head of the control block follows the kernels to pinned memory
+    GS_CUDA(cudaMemcpyAsync(r->head, r->arena, kCtlHead, cudaMemcpyDeviceToHost, r->st));
+    GS_CUDA(cudaEventRecord(r->ev2, r->st));
     r->ready = false;
     return GS_OK;
 }
@@ -113,9 +162,9 @@ gs_status enqueue(gs_result* r) {
 gs_status wait_result(gs_result* r) {
     if (r->ready) return GS_OK;
     for (int attempt = 0; attempt < kMaxRetries; ++attempt) {
-        GS_CUDA(cudaStreamSynchronize(r->st));
+        GS_CUDA(cudaEventSynchronize(r->ev2));
         Ctl head;
-        GS_CUDA(cudaMemcpy(&head, r->arena, kCtlHead, cudaMemcpyDeviceToHost));
+        std::memcpy(&head, r->head, kCtlHead);
         if (head.status & kStHuge) {
             set_error("gs_eval_query: the answer has more than 2^40 rows under one binding");
             return GS_ENOMEM;
@@ -179,8 +228,8 @@ void release(gs_result* r) {
         r->g->alloc.put(r->work, r->st);
         r->g->alloc.put(r->lists, r->st);
     }
-    if (r->ev0) cudaEventDestroy(r->ev0);
-    if (r->ev1) cudaEventDestroy(r->ev1);
+    const cudaEvent_t ev[3] = {r->ev0, r->ev1, r->ev2};
+    if (r->g) give_host_res(r->g, ev, r->head);
     delete r;
 }
 
@@ -335,7 +384,7 @@ gs_status gs::result_compact(gs_result* r) {
 
 gs_status gs::result_ready(gs_result* r, int* done) {
     if (r->ready) { *done = 1; return GS_OK; }
-    cudaError_t e = cudaEventQuery(r->ev1);
+    cudaError_t e = cudaEventQuery(r->ev2);
     if (e == cudaErrorNotReady) { *done = 0; return GS_OK; }
     if (e != cudaSuccess) return cuda_fail(e, "gs_eval_query");
     *done = 1;
@@ -365,8 +414,9 @@ gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_strea
     r->st = (cudaStream_t)cuda_stream;
     const uint64_t words = (g->N + 31) / 32;
     gs_status rc = GS_OK;
-    if (cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess) {
-        rc = cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    cudaEvent_t* ev[3] = {&r->ev0, &r->ev1, &r->ev2};
+    if (take_host_res(g, ev, &r->head) != GS_OK) {
+        rc = GS_ECUDA;
     }
     if (rc == GS_OK && plan->needs_scan) {
         r->bits = (uint32_t*)g->alloc.get(4 * words * std::max(1, plan->n_levels), r->st);
@@ -384,10 +434,9 @@ gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_strea
     // budget (then it would only hand the query back)
     r->mode = (small_eligible(plan) && !force_grid && first_level_bound(g, plan) <= kSmallRoute) ? 1 : 0;
     if (rc == GS_OK) {
-        size_t free_b = 0, total_b = 0;
-        cudaMemGetInfo(&free_b, &total_b);
-        uint64_t want = std::max<uint64_t>(kArenaMin, std::min<uint64_t>(kArenaDefault, free_b / 8));
-        if (r->mode == 1) want = kArenaSmall;
+        uint64_t want = kArenaSmall;
+        if (r->mode == 0)
+            want = std::max<uint64_t>(kArenaMin, std::min<uint64_t>(kArenaDefault, free_device_bytes(g) / 8));
         if (const char* env = getenv("GS_ARENA_BYTES")) {   // initial workspace size
             unsigned long long v = strtoull(env, nullptr, 10);
             if (v >= 4096) want = v;
@@ -494,6 +543,8 @@ void gs_free_graph(gs_graph* g) {
     free_store(g, nullptr);
     cudaDeviceSynchronize();
     for (int i = 0; i < g->n_side; ++i) cudaStreamDestroy(g->side[i]);
+    for (cudaEvent_t e : g->ev_free) cudaEventDestroy(e);
+    for (uint8_t* b : g->head_blocks) cudaFreeHost(b);
     delete g;
 }
 

@@ -9,13 +9,17 @@
 //                 the row / column of the bound end (a predicate-filtered
 //                 row selection, Eq. 15 / Eq. 19 / Eq. 23 for one node), and
 //                 the shortest of them;
-//   scan          exclusive offsets of the candidate counts;
+//                 Its blocks also scan their counts into block-local
+//                 offsets, and the last block to finish turns the block
+//                 sums into block offsets and the level's candidate total;
 //   k_expand      load-balanced over all candidates: take the candidate from
 //                 the shortest range, keep it when it is in every other
 //                 binder range, passes the pre-pruning tests of Sec. 7.2.2
 //                 (candidate vector or predicate presence) and its
 //                 self-loops; survivors are appended with warp-aggregated
 //                 atomics.
+// Consecutive kernels are chained with programmatic dependent launch: each
+// is scheduled while the one before it runs and waits for it on entry.
 // A parent without candidates has no children, so dead bindings never
 // reach later levels (pre-pruning). Leaves (variables with one pattern)
 // are not materialized: k_enum_range stores their range per last-level
@@ -36,7 +40,9 @@ namespace gs {
 
 __global__ void k_init(ExecDev E, ConstChecks cc) {
     Ctl* c = E.ctl;
-    if (threadIdx.x == 0 && blockIdx.x == 0) c->one = 1;
+    for (uint32_t i = threadIdx.x; i < kCtlHead / 8; i += blockDim.x) ((uint64_t*)c)[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) c->one = 1;
     for (uint32_t i = threadIdx.x; i < cc.n; i += blockDim.x) {
         uint32_t s = cc.t[3 * i], p = cc.t[3 * i + 1], o = cc.t[3 * i + 2];
         uint32_t lo, len;
@@ -45,9 +51,11 @@ __global__ void k_init(ExecDev E, ConstChecks cc) {
     }
 }
 
-// Candidate counts of the parent nodes of level l.
+// Candidate counts of the parent nodes of level l, as block-local
+// exclusive offsets; the last block writes the block offsets and the total.
 __global__ void __launch_bounds__(kThreads) k_range(ExecDev E, int l, LevelSpec L) {
-    const Ctl* ctl = E.ctl;
+    chain_enter();
+    Ctl* ctl = E.ctl;
     if (overflowed(ctl)) return;
     __shared__ const uint2* lv[kMaxLevels];
     load_levels(E, l - 1, lv);
@@ -60,15 +68,16 @@ __global__ void __launch_bounds__(kThreads) k_range(ExecDev E, int l, LevelSpec 
         return;
     }
     const bool dead = ctl->dead != 0;
-    uint64_t beg, end;
-    block_chunk(np, blockIdx.x, gridDim.x, beg, end);
-    uint64_t sum = 0;
-    for (uint64_t i = beg + threadIdx.x; i < end; i += kThreads) {
+    const uint32_t sh = pow2_shift(np, gridDim.x);
+    const uint64_t beg = min((uint64_t)blockIdx.x << sh, np), end = min(beg + ((uint64_t)1 << sh), np);
+    uint64_t carry = 0;
+    for (uint64_t base = beg; base < end; base += kThreads) {
+        const uint64_t i = base + threadIdx.x;
         uint64_t cnt = 0;
         uint32_t sel = 0;
-        if (!dead) {
+        if (i < end && !dead) {
             if (L.src == kSrcList) {
-                cnt = E.ctl->list_n[l];
+                cnt = ctl->list_n[l];
             } else {
                 uint32_t vid[kMaxLevels];
                 if (l > 0) walk(lv, l - 1, (uint32_t)i, vid);
@@ -84,15 +93,20 @@ __global__ void __launch_bounds__(kThreads) k_range(ExecDev E, int l, LevelSpec 
                 cnt = best;
             }
         }
-        S.roff[i] = cnt;
-        S.sel[i] = (uint8_t)sel;
-        sum += cnt;
+        uint64_t t;
+        const uint64_t ex = block_excl_scan_u64(cnt, &t);
+        if (i < end) {
+            S.roff[i] = carry + ex;
+            S.sel[i] = (uint8_t)sel;
+        }
+        carry += t;
     }
-    sum = block_sum_u64(sum);
-    if (threadIdx.x == 0) E.ctl->bsum[blockIdx.x] = sum;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->roff_shift = sh;
+    arrive_and_scan(ctl, carry, &ctl->cand);
 }
 
 __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec L) {
+    chain_enter();
     Ctl* ctl = E.ctl;
     if (overflowed(ctl)) return;
     __shared__ uint64_t tile_nodes[2];
@@ -100,6 +114,7 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
     const uint32_t nbm = L.n_binders > 0 ? L.n_binders : 1;
     Scratch S = scratch_at(E, np, nbm);
     const uint64_t T = ctl->cand;
+    const uint32_t sh = ctl->roff_shift;
     uint64_t base_l = kCtlBytes;
     for (int j = 0; j < l; ++j) base_l += align256(8ull * ctl->n[j]);
     const uint64_t cap = S.base > base_l ? (S.base - base_l) / 8 : 0;
@@ -108,8 +123,8 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
     for (uint64_t t0 = (uint64_t)blockIdx.x * kExpTile; t0 < T; t0 += (uint64_t)gridDim.x * kExpTile) {
         uint64_t t1 = min(t0 + kExpTile, T);
         if (threadIdx.x == 0) {
-            tile_nodes[0] = upper_bound_u64(S.roff, 0, np, t0) - 1;
-            tile_nodes[1] = upper_bound_u64(S.roff, tile_nodes[0], np, t1 - 1);
+            tile_nodes[0] = upper_bound_roff(S.roff, ctl, sh, 0, np, t0) - 1;
+            tile_nodes[1] = upper_bound_roff(S.roff, ctl, sh, tile_nodes[0], np, t1 - 1);
         }
         __syncthreads();
         const uint64_t i0 = tile_nodes[0], i1 = tile_nodes[1];
@@ -118,9 +133,9 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
             bool keep = false;
             uint32_t x = 0, node = 0;
             if (q < t1) {
-                uint64_t i = upper_bound_u64(S.roff, i0, i1, q) - 1;
+                uint64_t i = upper_bound_roff(S.roff, ctl, sh, i0, i1, q) - 1;
                 node = (uint32_t)i;
-                uint64_t j = q - S.roff[i];
+                uint64_t j = q - roff_at(S.roff, ctl, sh, i);
                 uint32_t sel = S.sel[i];
                 const uint2* rng = S.rng + i * nbm;
                 if (L.src == kSrcList) {
@@ -137,30 +152,13 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
     }
 }
 
-// In-place exclusive scan of the candidate counts in the scratch of level l
-// (np = *np_ptr parents, nbm binder slots).
-__global__ void __launch_bounds__(kThreads) k_scan_apply_scratch(ExecDev E, const uint64_t* np_ptr,
-                                                                 uint32_t nbm) {
-    const Ctl* ctl = E.ctl;
-    if (overflowed(ctl) || (ctl->status & kStHuge)) return;
-    const uint64_t np = *np_ptr;
-    Scratch S = scratch_at(E, np, nbm);
-    uint64_t beg, end;
-    block_chunk(np, blockIdx.x, gridDim.x, beg, end);
-    uint64_t carry = ctl->boff[blockIdx.x];
-    for (uint64_t base = beg; base < end; base += kThreads) {
-        uint64_t i = base + threadIdx.x;
-        uint64_t v = i < end ? S.roff[i] : 0, t;
-        uint64_t ex = block_excl_scan_u64(v, &t);
-        if (i < end) S.roff[i] = carry + ex;
-        carry += t;
-    }
-}
-
 // ------------------------------------------------------------------ //
 // Candidate vector -> ordered vertex list (warp ballot / popc + block scan).
 
+// Per-block counts of the candidate vector's vertices; the last block writes
+// the block offsets and the total (level 0's size, or the list length).
 __global__ void __launch_bounds__(kThreads) k_bits_count(ExecDev E, int l, LevelSpec L) {
+    chain_enter();
     if (overflowed(E.ctl)) return;
     const uint32_t* bm = E.bits + (uint64_t)l * E.words;
     uint64_t beg, end;
@@ -170,11 +168,12 @@ __global__ void __launch_bounds__(kThreads) k_bits_count(ExecDev E, int l, Level
         for (uint64_t w = beg + threadIdx.x; w < end; w += kThreads)
             c += __popc(word_keep(E, L, (uint32_t)w, bm[w]));
     c = block_sum_u64(c);
-    if (threadIdx.x == 0) E.ctl->bsum[blockIdx.x] = c;
+    arrive_and_scan(E.ctl, c, l == 0 ? &E.ctl->n[0] : &E.ctl->list_n[l]);
 }
 
 // to_level: write (vertex, 0) pairs as level l (a root); else the list of level l
 __global__ void __launch_bounds__(kThreads) k_bits_write(ExecDev E, int l, LevelSpec L, int to_level) {
+    chain_enter();
     Ctl* ctl = E.ctl;
     if (overflowed(ctl) || ctl->dead) return;
     const uint32_t* bm = E.bits + (uint64_t)l * E.words;
@@ -210,7 +209,11 @@ __global__ void __launch_bounds__(kThreads) k_bits_write(ExecDev E, int l, Level
 
 constexpr uint64_t kCountCap = 1ull << 40;
 
+// Answer rows per last-level node (the product of its leaf ranges), as
+// block-local exclusive offsets; the last block writes the block offsets and
+// the row total.
 __global__ void __launch_bounds__(kThreads) k_enum_range(ExecDev E, int last, EnumSpec F) {
+    chain_enter();
     Ctl* ctl = E.ctl;
     if (overflowed(ctl)) return;
     __shared__ const uint2* lv[kMaxLevels];
@@ -222,12 +225,13 @@ __global__ void __launch_bounds__(kThreads) k_enum_range(ExecDev E, int last, En
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->status, kStOverflow);
         return;
     }
-    uint64_t beg, end;
-    block_chunk(n, blockIdx.x, gridDim.x, beg, end);
-    uint64_t sum = 0;
-    for (uint64_t i = beg + threadIdx.x; i < end; i += kThreads) {
-        uint64_t cnt = 1;
-        if (F.n_leaves > 0) {
+    const uint32_t sh = pow2_shift(n, gridDim.x);
+    const uint64_t beg = min((uint64_t)blockIdx.x << sh, n), end = min(beg + ((uint64_t)1 << sh), n);
+    uint64_t carry = 0;
+    for (uint64_t base = beg; base < end; base += kThreads) {
+        const uint64_t i = base + threadIdx.x;
+        uint64_t cnt = i < end ? 1 : 0;
+        if (i < end && F.n_leaves > 0) {
             uint32_t vid[kMaxLevels];
             walk(lv, last, (uint32_t)i, vid);
             for (int j = 0; j < F.n_leaves; ++j) {
@@ -239,11 +243,13 @@ __global__ void __launch_bounds__(kThreads) k_enum_range(ExecDev E, int last, En
                 if (cnt > kCountCap) { cnt = kCountCap; atomicOr(&ctl->status, kStHuge); }
             }
         }
-        S.roff[i] = cnt;
-        sum += cnt;
+        uint64_t t;
+        const uint64_t ex = block_excl_scan_u64(cnt, &t);
+        if (i < end) S.roff[i] = carry + ex;
+        carry += t;
     }
-    sum = block_sum_u64(sum);
-    if (threadIdx.x == 0) ctl->bsum[blockIdx.x] = sum;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->roff_shift = sh;
+    arrive_and_scan(ctl, carry, &ctl->rows);
 }
 
 // Tiles of answer rows: consecutive threads take consecutive rows (their
@@ -254,6 +260,7 @@ constexpr uint32_t kEnumStageWords = 7168;    // 28 KB of staged rows
 constexpr uint32_t kEnumTileNodes = 2048;     // row offsets of a tile's nodes kept in shared memory
 
 __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, EnumSpec F) {
+    chain_enter();
     Ctl* ctl = E.ctl;
     if (overflowed(ctl) || (ctl->status & kStHuge)) return;
     __shared__ const uint2* lv[kMaxLevels];
@@ -265,6 +272,7 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
     const uint32_t nl = F.n_leaves > 0 ? F.n_leaves : 1;
     Scratch S = scratch_at(E, n, nl);
     const uint64_t T = ctl->rows;
+    const uint32_t sh = ctl->roff_shift;
     uint64_t out_off = kCtlBytes;
     for (int j = 0; j <= last; ++j) out_off += align256(8ull * ctl->n[j]);
     const uint32_t nv = (uint32_t)F.n_vars;
@@ -280,8 +288,8 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
     for (uint64_t t0 = (uint64_t)blockIdx.x * tile_rows; t0 < T; t0 += (uint64_t)gridDim.x * tile_rows) {
         const uint64_t t1 = min(t0 + tile_rows, T);
         if (threadIdx.x == 0) {
-            tile_nodes[0] = upper_bound_u64(S.roff, 0, n, t0) - 1;
-            tile_nodes[1] = upper_bound_u64(S.roff, tile_nodes[0], n, t1 - 1);
+            tile_nodes[0] = upper_bound_roff(S.roff, ctl, sh, 0, n, t0) - 1;
+            tile_nodes[1] = upper_bound_roff(S.roff, ctl, sh, tile_nodes[0], n, t1 - 1);
         }
         __syncthreads();
         const uint64_t i0 = tile_nodes[0], i1 = tile_nodes[1];
@@ -289,7 +297,8 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
         // node search then runs there
         const bool local = i1 - i0 <= kEnumTileNodes;
         if (local)
-            for (uint64_t k = threadIdx.x; k < i1 - i0; k += kThreads) roff_s[k] = S.roff[i0 + k];
+            for (uint64_t k = threadIdx.x; k < i1 - i0; k += kThreads)
+                roff_s[k] = roff_at(S.roff, ctl, sh, i0 + k);
         __syncthreads();
         for (uint64_t q = t0 + threadIdx.x; q < t1; q += kThreads) {
             uint64_t i, base;
@@ -302,8 +311,8 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
                 i = i0 + lo;
                 base = roff_s[lo];
             } else {
-                i = upper_bound_u64(S.roff, i0, i1, q) - 1;
-                base = S.roff[i];
+                i = upper_bound_roff(S.roff, ctl, sh, i0, i1, q) - 1;
+                base = roff_at(S.roff, ctl, sh, i);
             }
             uint64_t loc = q - base;
             // straight into the staged row: each level's and leaf's column
@@ -354,40 +363,30 @@ uint64_t host_level_off(const uint64_t* n, int l) {
 
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
                        cudaStream_t st) {
-    const int nb = g->n_blocks;
+    const dim3 nb(g->n_blocks), th(kThreads);
     Ctl* ctl = E.ctl;
-    GS_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
     ConstChecks cc{};
     cc.n = (uint32_t)(P->const_triples.size() / 3);
     if (cc.n > kMaxPatterns) cc.n = kMaxPatterns;
     for (uint32_t i = 0; i < 3 * cc.n; ++i) cc.t[i] = P->const_triples[i];
-    k_init<<<1, kThreads, 0, st>>>(E, cc);
+    k_init<<<1, kThreads, 0, st>>>(E, cc);   // zeroes the control block's head
     uint32_t nl_launch = 1;
     if (P->needs_scan) {
-        gs_status rc = run_scan(g, P->scan, E.bits, scan_work, st, &E.ctl->status);
+        gs_status rc = run_scan(g, P->scan, E.bits, scan_work, st, &ctl->status);
         if (rc != GS_OK) return rc;
-        nl_launch += 4;
+        nl_launch += 3;
     }
     for (int l = 0; l < P->n_levels; ++l) {
         const LevelSpec& L = P->levels[l];
         if (L.src == kSrcList) {
-            k_bits_count<<<nb, kThreads, 0, st>>>(E, l, L);
-            uint64_t* total = l == 0 ? &ctl->n[0] : &ctl->list_n[l];
-            k_scan_block_sums<<<1, kThreads, 0, st>>>(ctl->bsum, ctl->boff, nb, total, &ctl->status);
-            nl_launch += 3;
-            if (l == 0) {
-                k_bits_write<<<nb, kThreads, 0, st>>>(E, l, L, 1);
-                continue;
-            }
-            k_bits_write<<<nb, kThreads, 0, st>>>(E, l, L, 0);
+            GS_CUDA(launch_chained(k_bits_count, nb, th, 0, st, E, l, L));
+            GS_CUDA(launch_chained(k_bits_write, nb, th, 0, st, E, l, L, l == 0 ? 1 : 0));
+            nl_launch += 2;
+            if (l == 0) continue;
         }
-        nl_launch += 4;
-        const uint64_t* np_ptr = l == 0 ? &ctl->one : &ctl->n[l - 1];
-        const uint32_t nbm = L.n_binders > 0 ? L.n_binders : 1;
-        k_range<<<nb, kThreads, 0, st>>>(E, l, L);
-        k_scan_block_sums<<<1, kThreads, 0, st>>>(ctl->bsum, ctl->boff, nb, &ctl->cand, &ctl->status);
-        k_scan_apply_scratch<<<nb, kThreads, 0, st>>>(E, np_ptr, nbm);
-        k_expand<<<nb, kThreads, 0, st>>>(E, l, L);
+        GS_CUDA(launch_chained(k_range, nb, th, 0, st, E, l, L));
+        GS_CUDA(launch_chained(k_expand, nb, th, 0, st, E, l, L));
+        nl_launch += 2;
     }
     const int last = P->n_levels - 1;
     EnumSpec F{};
@@ -397,12 +396,9 @@ gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, vo
     for (int v = 0; v < P->n_vars; ++v) F.var_src[v] = P->var_src[v];
     for (int l = 0; l < P->n_levels; ++l) F.col_of_level[l] = P->levels[l].var;
     for (int j = 0; j < P->n_leaves; ++j) F.col_of_leaf[j] = P->leaves[j].var;
-    const uint32_t nl = P->n_leaves > 0 ? P->n_leaves : 1;
-    k_enum_range<<<nb, kThreads, 0, st>>>(E, last, F);
-    k_scan_block_sums<<<1, kThreads, 0, st>>>(ctl->bsum, ctl->boff, nb, &ctl->rows, &ctl->status);
-    k_scan_apply_scratch<<<nb, kThreads, 0, st>>>(E, &ctl->n[last], nl);
-    k_enum_write<<<nb, kThreads, 0, st>>>(E, last, F);
-    nl_launch += 4;
+    GS_CUDA(launch_chained(k_enum_range, nb, th, 0, st, E, last, F));
+    GS_CUDA(launch_chained(k_enum_write, nb, th, 0, st, E, last, F));
+    nl_launch += 2;
     if (launches) *launches = nl_launch;
     GS_CUDA(cudaGetLastError());
     return GS_OK;

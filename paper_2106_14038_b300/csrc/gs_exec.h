@@ -18,6 +18,8 @@ struct Ctl {
     uint64_t rows;                 // answer rows
     uint32_t status;               // kSt* bits
     uint32_t dead;                 // a pattern with two constant ends has no match
+    uint32_t arrive;               // blocks of the running count kernel that are done
+    uint32_t roff_shift;           // its blocks took 2^roff_shift consecutive items each
     uint64_t bsum[kBlocks];
     uint64_t boff[kBlocks];
 };

@@ -118,6 +118,71 @@ __device__ __forceinline__ uint64_t upper_bound_u64(const uint64_t* a, uint64_t 
     return lo;
 }
 
+// Count kernels split n items into blocks of 2^shift consecutive items (a
+// power of two: a consumer finds an item's block with a shift).
+__device__ __forceinline__ uint32_t pow2_shift(uint64_t n, uint32_t nb) {
+    const uint64_t chunk = (n + nb - 1) / nb;
+    uint32_t s = 0;
+    while ((1ull << s) < chunk) ++s;
+    return s;
+}
+
+// End of a count kernel, called by every thread of every block: the block
+// hands in its sum; the last block to arrive turns the sums into exclusive
+// block offsets (ctl->boff) and writes the total. No block waits for
+// another. The counter is left at zero for the next count kernel.
+__device__ __forceinline__ void arrive_and_scan(Ctl* ctl, uint64_t block_total, uint64_t* total) {
+    __shared__ uint32_t last;
+    if (threadIdx.x == 0) {
+        ctl->bsum[blockIdx.x] = block_total;
+        __threadfence();   // the sum (and the block's other writes) before the count
+        last = atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();       // acquire: every block's sum
+    uint64_t carry = 0;
+    for (uint32_t base = 0; base < gridDim.x; base += kThreads) {
+        const uint32_t i = base + threadIdx.x;
+        const uint64_t v = i < gridDim.x ? __ldcg((const unsigned long long*)&ctl->bsum[i]) : 0;
+        uint64_t t;
+        const uint64_t ex = block_excl_scan_u64(v, &t);
+        if (i < gridDim.x) ctl->boff[i] = carry + ex;
+        carry += t;
+    }
+    if (threadIdx.x == 0) {
+        *total = carry;
+        ctl->arrive = 0;
+    }
+}
+
+// Global exclusive offset of item i of a count kernel's output: its offset
+// within its block plus the block's offset.
+__device__ __forceinline__ uint64_t roff_at(const uint64_t* roff, const Ctl* ctl, uint32_t sh,
+                                            uint64_t i) {
+    return roff[i] + ctl->boff[i >> sh];
+}
+
+// First i in [lo, hi) with roff_at(i) > key (hi when none).
+__device__ __forceinline__ uint64_t upper_bound_roff(const uint64_t* roff, const Ctl* ctl,
+                                                     uint32_t sh, uint64_t lo, uint64_t hi,
+                                                     uint64_t key) {
+    while (lo < hi) {
+        const uint64_t mid = lo + ((hi - lo) >> 1);
+        if (roff_at(roff, ctl, sh, mid) <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Programmatic dependent launch: a kernel of the chain lets the next one be
+// scheduled at once and waits, before its first access to memory, for the
+// one before it to finish (a no-op for a kernel launched without the
+// attribute).
+__device__ __forceinline__ void chain_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ bool self_ok(const ExecDev& E, const LevelSpec& L, uint32_t x) {
     for (int j = 0; j < L.n_self; ++j) {
         uint32_t lo, len;

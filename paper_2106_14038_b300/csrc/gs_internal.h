@@ -4,7 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -45,6 +47,26 @@ gs_status cuda_fail(cudaError_t e, const char* what);
         cudaError_t _e = (call);                                 \
         if (_e != cudaSuccess) return ::gs::cuda_fail(_e, #call); \
     } while (0)
+
+// Launch with programmatic stream serialization: the kernel may be
+// scheduled while the previous kernel in the stream is still running; it
+// must wait for that one (griddepcontrol.wait) before touching what it
+// writes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                           cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // Device memory through the caller's hook or stream-ordered cudaMallocAsync.
 struct Alloc {
@@ -99,6 +121,14 @@ struct gs_graph {
     // queries whose first level is certainly large away from the
     // single-CTA evaluator
     std::vector<uint32_t> deg_out, deg_in;
+    // per-query host resources kept for reuse: timing events and pinned
+    // slots the control-block head of a result is copied into
+    std::mutex res_mu;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<uint8_t*> head_free;
+    std::vector<uint8_t*> head_blocks;
+    uint64_t free_seen = 0;   // free device memory at free_seen_at
+    std::chrono::steady_clock::time_point free_seen_at{};
 };
 
 namespace gs {

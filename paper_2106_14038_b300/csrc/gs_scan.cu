@@ -420,25 +420,6 @@ size_t scan_work_bytes(const gs_graph* g) {
     return 8ull * mask_words(g->N) + 512;
 }
 
-// Launch with programmatic stream serialization: the kernel may start
-// while the previous one in the stream finishes; it waits for it with
-// griddepcontrol.wait before touching what that one writes.
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                                    cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
-
 template <typename LutT>
 static gs_status launch_scan(const gs_graph* g, const ScanDev& sd, uint32_t* mask_out,
                              uint32_t* mask_in, uint32_t* status, uint32_t warps, cudaStream_t st) {
@@ -453,7 +434,7 @@ static gs_status launch_scan(const gs_graph* g, const ScanDev& sd, uint32_t* mas
     const uint32_t grid = std::max(1u, std::min((uint32_t)g->sm_count, (n_items + warps - 1) / warps));
     const ScanSide out{dview(g->out), g->out.heads, g->out.items, g->out.n_items, mask_out};
     const ScanSide in{dview(g->in), g->in.heads, g->in.items, g->in.n_items, mask_in};
-    GS_CUDA(launch_dependent(k_scan<LutT>, dim3(grid), dim3(warps * 32), smem, st, out, in, g->N,
+    GS_CUDA(launch_chained(k_scan<LutT>, dim3(grid), dim3(warps * 32), smem, st, out, in, g->N,
                              g->P, sd, status));
     return GS_OK;
 }
@@ -489,7 +470,7 @@ gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void
         rc = launch_scan<uint8_t>(g, sd, mask_out, mask_in, status, w8, st);
     if (rc != GS_OK) return rc;
     const uint32_t eb = std::min<uint32_t>((words + 31) / 32, (uint32_t)g->sm_count * 8);
-    GS_CUDA(launch_dependent(k_scan_eval, dim3(std::max(1u, eb)), dim3(kThreads), 0, st,
+    GS_CUDA(launch_chained(k_scan_eval, dim3(std::max(1u, eb)), dim3(kThreads), 0, st,
                              (const uint32_t*)mask_out, (const uint32_t*)mask_in, g->N, sd, bits,
                              words));
     GS_CUDA(cudaGetLastError());

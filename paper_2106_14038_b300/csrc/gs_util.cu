@@ -28,7 +28,15 @@ gs_status cuda_fail(cudaError_t e, const char* what) {
 
 void* Alloc::get(size_t bytes, cudaStream_t st) const {
     if (bytes == 0) bytes = 256;
-    if (has_hook) return hook.alloc(bytes, (void*)st, hook.ctx);
+    if (has_hook) {
+        // the bulk copies and 16-byte accesses rely on cudaMalloc's alignment
+        void* p = hook.alloc(bytes, (void*)st, hook.ctx);
+        if (p && ((uintptr_t)p & 255u)) {
+            hook.free(p, (void*)st, hook.ctx);
+            return nullptr;
+        }
+        return p;
+    }
     void* p = nullptr;
     if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
         cudaGetLastError();

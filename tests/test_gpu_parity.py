@@ -411,6 +411,35 @@ def test_allocation_failure_is_a_status(rmat14, fail_after):
     assert np.array_equal(g_ok.query(pats), ix.eval(pats))
 
 
+def test_allocator_alignment_is_checked(rmat14):
+    # a hook whose blocks start 16 bytes past a 256-byte boundary: the first
+    # such block goes straight back to the hook and the build fails as out
+    # of memory, with nothing left allocated
+    import torch
+    w, (s, p, o), g_ok, ix = rmat14
+    live = {}
+
+    def _alloc(nbytes, stream, ctx):
+        base = torch.cuda.caching_allocator_alloc(int(nbytes) + 256, 0, stream)
+        live[base + 16] = base
+        return base + 16
+
+    def _free(ptr, stream, ctx):
+        if ptr:
+            torch.cuda.caching_allocator_delete(live.pop(ptr))
+
+    alloc = gs.TorchAllocator()
+    alloc._cb_alloc = gs._ALLOC_FN(_alloc)
+    alloc._cb_free = gs._FREE_FN(_free)
+    alloc.struct = gs._Allocator(alloc._cb_alloc, alloc._cb_free, None)
+    with pytest.raises(gs.GsError) as e:
+        gs.Graph(s, p, o, w.n_vertices, w.n_preds, allocator=alloc)
+    assert e.value.status == 2
+    assert not live
+    pats = [(-1, 2, -2)]
+    assert np.array_equal(g_ok.query(pats), ix.eval(pats))
+
+
 def test_server_answers_equal_alone(rmat14):
     # continuous batching: the same queries submitted together, interleaved
     # and repeated; every answer equals the query evaluated alone (and the
