@@ -307,9 +307,9 @@ gs_status gs_scan_candidates(gs_graph* g, const uint32_t* preds, const uint8_t* 
  * paper has no counterpart; it is an engineering variant for callers that
  * must not allocate). Same arguments, result and errors as
  * gs_scan_candidates, plus:
- *   - the scan's workspace, a little over 8 (N + 8) bytes for a graph of N
- *     vertices, lives in one static device array of
- *     gs_noalloc_scratch_bytes() bytes (48 MiB: graphs up to about 6
+ *   - the scan's workspace, a little over 4 (N + 256) bytes for a graph of
+ *     N vertices, lives in one static device array of
+ *     gs_noalloc_scratch_bytes() bytes (48 MiB: graphs up to about 12
  *     million vertices); a graph that needs more gets GS_EINVAL and a
  *     message naming both sizes;
  *   - nothing in that array has to start at zero (each call zeroes what it

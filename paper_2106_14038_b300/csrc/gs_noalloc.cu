@@ -5,10 +5,10 @@
 // allocate device memory on the call path.
 //
 // Scratch: kNoAllocScratchBytes in the file-scope array below. The call
-// needs scan_work_bytes(g) of it (a little over 8 (N + 8) bytes) and
+// needs scan_work_bytes(g) of it (a little over 4 (N + 256) bytes) and
 // rejects graphs that need more. Nothing in the array has to start at
-// zero: the first kernel of every call zeroes every slot the scan ORs into
-// and its work counters; all other masks are written before they are read.
+// zero: the first kernel of every call zeroes every word the scan ORs into
+// and the status word; all other masks are written before they are read.
 //
 // Set-up: the first call on a device looks the array's address up with
 // cudaGetSymbolAddress (which may load this module) and caches it; make

@@ -14,7 +14,7 @@
 //   2. k_scan_eval combines the two masks per vertex and writes one bit per
 //      variable into the candidate vectors (warp ballot -> one word per 32
 //      vertices, so the vectors need no clearing).
-// k_scan_zero first clears the mask slots that several items OR into; each
+// k_scan_zero first clears the mask words that several items OR into; each
 // kernel is launched to overlap the tail of the one before it
 // (programmatic dependent launch) and waits for it where it must.
 //
@@ -33,10 +33,13 @@
 //      lanes then gives, per lane, the OR of the row running through the
 //      lane's end;
 //   B. rows phase: one lane per row combines its last position's value with
-//      the previous lane's running total and writes the row's mask; a row
-//      that crosses an item boundary is ORed into its (zeroed) slot instead.
+//      the previous lane's running total and writes the row's mask; rows in
+//      the 32-bit words of the item's first and last rows (which a
+//      neighbouring item may also write) are ORed into those zeroed words.
 // Bytes moved: per orientation 4(N+1) row pointers + 4M labels + M/8
-// row-start bits, a 4N mask written and read once, and N/8 per vector.
+// row-start bits, a 2N mask (16-bit slots) written and read once, and N/8
+// per vector. The streamed inputs are read with an evict-first L2 policy,
+// so the masks tend to stay in L2 until k_scan_eval reads them.
 #include <algorithm>
 
 #include "gs_device.cuh"
@@ -106,14 +109,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
-// Global -> shared bulk copy; both addresses 16-byte aligned, bytes a
-// multiple of 16.
+// L2 policy for data read once: its lines are the first to be evicted.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// Global -> shared bulk copy under L2 policy pol; both addresses 16-byte
+// aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
+                                         uint64_t* bar, uint64_t pol) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
 
@@ -141,8 +151,8 @@ __device__ __forceinline__ ItemLayout item_layout(uint4 d) {
 }
 
 // Lanes 0..2 of a warp put item d into buf behind bar, one region each,
-// with one copy instruction; lane 0 first announces the bytes. Called by
-// the whole warp.
+// with one copy instruction (evict-first: every word is read once); lane 0
+// first announces the bytes. Called by the whole warp.
 __device__ __forceinline__ void issue_item(uint32_t lane, uint32_t* buf, uint64_t* bar, uint4 d,
                                            const DStore& S, const uint32_t* heads) {
     const ItemLayout L = item_layout(d);
@@ -153,7 +163,7 @@ __device__ __forceinline__ void issue_item(uint32_t lane, uint32_t* buf, uint64_
                                     : S.ptr + (d.x & ~3u);
     const uint32_t off = lane == 0 ? 0u : lane == 1 ? L.ho : L.po;
     const uint32_t n = lane == 0 ? L.nl : lane == 1 ? L.nh : L.np;
-    if (lane < 3 && n) bulk_g2s(buf + off, src, 4u * n, bar);
+    if (lane < 3 && n) bulk_g2s(buf + off, src, 4u * n, bar, evict_first_policy());
 }
 
 // label -> one-hot slot bit of this direction's query predicates
@@ -193,7 +203,7 @@ struct ScanSide {
     const uint32_t* heads;
     const uint2* items;
     uint32_t n_items;
-    uint32_t* mask;   // per vertex: the query predicates of this direction its row holds
+    uint16_t* mask;   // per vertex: the query predicates of this direction its row holds
 };
 
 // Both orientations in one grid: items 0 .. out.n_items - 1 are the CSR's,
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
         const uint4 d = desc[warp][b];
         const uint32_t cols = side_of[warp][b];
         const LutT* lut = luts + (cols ? P + 2 : 0u);
-        uint32_t* mask = cols ? in.mask : out.mask;
+        uint16_t* mask = cols ? in.mask : out.mask;
         const uint32_t r0 = d.x, k0 = d.y, r1 = d.z, k1 = d.w;
         const ItemLayout L = item_layout(d);
         const uint32_t* buf = bufs + b * kBufWords;
@@ -334,8 +344,14 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
                 const uint32_t la = (lo - k0) / kScanLabPer, lb = (hi - 1 - k0) / kScanLabPer;
                 m = pm[hi - 1 - k0] | (lb > la ? cont[lb - 1] : 0u);
             }
-            if (r < r1 && s >= k0) mask[r] = m;     // the row lies in this item
-            else if (m) atomicOr(mask + r, m);       // it crosses an item boundary
+            // rows sharing a 32-bit word with r0 or r1 (zeroed by
+            // k_scan_zero) may be written by two items: ORed in whole words;
+            // every other row lies in this item alone
+            if ((r >> 1) == (r0 >> 1) || (r >> 1) == (r1 >> 1)) {
+                if (m) atomicOr(reinterpret_cast<uint32_t*>(mask) + (r >> 1), m << (16 * (r & 1u)));
+            } else {
+                mask[r] = (uint16_t)m;
+            }
         }
         __syncwarp();   // buffer b and pm are free again
         if (cn < n_items) {
@@ -362,67 +378,65 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
     }
 }
 
-// The mask slots of rows that cross item boundaries start at zero: the
-// items OR their parts into them.
-__global__ void k_scan_zero(const uint32_t* __restrict__ ptr_out, const uint2* __restrict__ items_out,
-                            uint32_t n_out, const uint32_t* __restrict__ ptr_in,
+// The 32-bit mask words holding an item's first row (so also the last row
+// of the item before) start at zero: the items OR their rows into them.
+__global__ void k_scan_zero(const uint2* __restrict__ items_out, uint32_t n_out,
                             const uint2* __restrict__ items_in, uint32_t n_in,
                             uint32_t* __restrict__ mask_out, uint32_t* __restrict__ mask_in,
                             uint32_t* __restrict__ status) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // k_scan may start its copies
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    for (uint32_t c = 1 + t; c < n_out; c += stride) {
-        const uint2 it = items_out[c];
-        if (ptr_out[it.x] < it.y) mask_out[it.x] = 0;
-    }
-    for (uint32_t c = 1 + t; c < n_in; c += stride) {
-        const uint2 it = items_in[c];
-        if (ptr_in[it.x] < it.y) mask_in[it.x] = 0;
-    }
+    for (uint32_t c = t; c <= n_out; c += stride) mask_out[items_out[c].x >> 1] = 0;
+    for (uint32_t c = t; c <= n_in; c += stride) mask_in[items_in[c].x >> 1] = 0;
     if (t == 0 && status) *status = 0;
 }
 
 // Candidate bits: vertex v is a candidate of variable u when its row holds
 // every out-predicate and its column every in-predicate u needs (Eq. 21).
-// A warp takes 128 vertices at a time, four per lane (16-byte loads of
-// both masks); the 4-bit groups of 8 lanes are ORed into one word.
-__global__ void k_scan_eval(const uint32_t* __restrict__ mask_out,
-                            const uint32_t* __restrict__ mask_in, uint32_t N, ScanDev sd,
+// A warp takes 256 vertices at a time, eight per lane (16-byte loads of
+// both 16-bit masks); the bytes of 4 lanes are ORed into one word.
+__global__ void k_scan_eval(const uint16_t* __restrict__ mask_out,
+                            const uint16_t* __restrict__ mask_in, uint32_t N, ScanDev sd,
                             uint32_t* __restrict__ bits, uint32_t words) {
     asm volatile("griddepcontrol.wait;" ::: "memory");   // the masks of k_scan
     const uint32_t lane = lane_id();
     const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g * 128 < N; g += warps) {
-        const uint32_t v = g * 128 + lane * 4;   // masks hold N + 8 words: the load stays inside
-        const uint4 mo = __ldcs(reinterpret_cast<const uint4*>(mask_out + v));
-        const uint4 mi = __ldcs(reinterpret_cast<const uint4*>(mask_in + v));
+    for (uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g * 256 < N; g += warps) {
+        const uint32_t v = g * 256 + lane * 8;   // masks hold N + 256 slots: the load stays inside
+        const uint4 mo4 = __ldcs(reinterpret_cast<const uint4*>(mask_out + v));
+        const uint4 mi4 = __ldcs(reinterpret_cast<const uint4*>(mask_in + v));
+        const uint32_t mo[4] = {mo4.x, mo4.y, mo4.z, mo4.w};
+        const uint32_t mi[4] = {mi4.x, mi4.y, mi4.z, mi4.w};
         for (uint32_t u = 0; u < sd.n_bvars; ++u) {
-            uint32_t nib = (eval_bits(sd, mo.x, mi.x, u) && v < N) |
-                           ((eval_bits(sd, mo.y, mi.y, u) && v + 1 < N) << 1) |
-                           ((eval_bits(sd, mo.z, mi.z, u) && v + 2 < N) << 2) |
-                           ((eval_bits(sd, mo.w, mi.w, u) && v + 3 < N) << 3);
-            uint32_t word = nib << (4 * (lane & 7));
+            uint32_t byte = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {   // vertices v + 2j (low half), v + 2j + 1 (high)
+                byte |= (uint32_t)(eval_bits(sd, mo[j] & 0xffffu, mi[j] & 0xffffu, u) &&
+                                   v + 2 * j < N) << (2 * j);
+                byte |= (uint32_t)(eval_bits(sd, mo[j] >> 16, mi[j] >> 16, u) &&
+                                   v + 2 * j + 1 < N) << (2 * j + 1);
+            }
+            uint32_t word = byte << (8 * (lane & 3));
             word |= __shfl_xor_sync(0xffffffffu, word, 1);
             word |= __shfl_xor_sync(0xffffffffu, word, 2);
-            word |= __shfl_xor_sync(0xffffffffu, word, 4);
-            const uint32_t wi = g * 4 + (lane >> 3);
-            if ((lane & 7) == 0 && wi < words) bits[(uint64_t)u * words + wi] = word;
+            const uint32_t wi = g * 8 + (lane >> 2);
+            if ((lane & 3) == 0 && wi < words) bits[(uint64_t)u * words + wi] = word;
         }
     }
 }
 
-// Workspace: mask_out | mask_in (N + 128 words each, 16-byte aligned) |
-// status word.
-static uint64_t mask_words(uint32_t N) { return ((uint64_t)N + 128 + 3) & ~3ull; }
+// Workspace: mask_out | mask_in (N + 256 16-bit slots each, 16-byte
+// aligned) | status word.
+static uint64_t mask_slots(uint32_t N) { return ((uint64_t)N + 256 + 7) & ~7ull; }
 
 size_t scan_work_bytes(const gs_graph* g) {
-    return 8ull * mask_words(g->N) + 512;
+    return 4ull * mask_slots(g->N) + 512;
 }
 
 template <typename LutT>
-static gs_status launch_scan(const gs_graph* g, const ScanDev& sd, uint32_t* mask_out,
-                             uint32_t* mask_in, uint32_t* status, uint32_t warps, cudaStream_t st) {
+static gs_status launch_scan(const gs_graph* g, const ScanDev& sd, uint16_t* mask_out,
+                             uint16_t* mask_in, uint32_t* status, uint32_t warps, cudaStream_t st) {
     const size_t smem = scan_smem_bytes<LutT>(g->P, warps);
     static size_t smem_set = 0;
     if (smem > smem_set) {
@@ -451,14 +465,15 @@ gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void
         sd.need_out[u] = spec.need_out[u];
         sd.need_in[u] = spec.need_in[u];
     }
-    uint32_t* mask_out = (uint32_t*)work;
-    uint32_t* mask_in = mask_out + mask_words(g->N);
+    uint16_t* mask_out = (uint16_t*)work;
+    uint16_t* mask_in = mask_out + mask_slots(g->N);
     const bool own = status == nullptr;
-    if (own) status = mask_in + mask_words(g->N);
+    if (own) status = reinterpret_cast<uint32_t*>(mask_in + mask_slots(g->N));
     const uint32_t words = (g->N + 31) / 32;
     const int nb = g->n_blocks;
-    k_scan_zero<<<nb, kThreads, 0, st>>>(g->out.ptr, g->out.items, g->out.n_items, g->in.ptr,
-                                         g->in.items, g->in.n_items, mask_out, mask_in,
+    k_scan_zero<<<nb, kThreads, 0, st>>>(g->out.items, g->out.n_items, g->in.items, g->in.n_items,
+                                         reinterpret_cast<uint32_t*>(mask_out),
+                                         reinterpret_cast<uint32_t*>(mask_in),
                                          own ? status : nullptr);
     // the 16-bit one-hot table unless it costs more than a few warps
     const uint32_t w16 = scan_warps_fit(g->P, sizeof(uint16_t));
@@ -469,9 +484,9 @@ gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void
     else
         rc = launch_scan<uint8_t>(g, sd, mask_out, mask_in, status, w8, st);
     if (rc != GS_OK) return rc;
-    const uint32_t eb = std::min<uint32_t>((words + 31) / 32, (uint32_t)g->sm_count * 8);
+    const uint32_t eb = std::min<uint32_t>((words + 63) / 64, (uint32_t)g->sm_count * 8);
     GS_CUDA(launch_chained(k_scan_eval, dim3(std::max(1u, eb)), dim3(kThreads), 0, st,
-                             (const uint32_t*)mask_out, (const uint32_t*)mask_in, g->N, sd, bits,
+                             (const uint16_t*)mask_out, (const uint16_t*)mask_in, g->N, sd, bits,
                              words));
     GS_CUDA(cudaGetLastError());
     return GS_OK;

@@ -66,7 +66,7 @@ def test_noalloc_rejects_a_graph_beyond_the_static_workspace():
     import torch
     limit = gs.load_library().gs_noalloc_scratch_bytes()
     assert limit == 48 << 20
-    n_v = limit // 8 + 1                    # 8 (N + 8) bytes alone exceed the area
+    n_v = limit // 4 + 1                    # 4 (N + 256) bytes alone exceed the area
     s = np.array([0, 1, n_v - 1], np.uint32)
     p = np.array([1, 2, 1], np.uint32)
     o = np.array([1, 2, 0], np.uint32)
