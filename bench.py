@@ -41,13 +41,18 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the CPU oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="plain", choices=["plain", "scan", "batched", "served"],
+    ap.add_argument("--mode", default="plain",
+                    choices=["plain", "scan", "batched", "served", "query"],
                     help="plain: the workload's queries one at a time (the headline line); "
                          "scan: the triple scan alone; batched: the batched workload "
                          "(rmat24: 4,096 queries in one launch) against one at a time; "
-                         "served: Poisson arrivals into the server on the scale-26 graph")
+                         "served: Poisson arrivals into the server on the scale-26 graph; "
+                         "query: the workload queries --query picks, one at a time (for "
+                         "profiling single kernels)")
     ap.add_argument("--queries", type=int, default=0,
                     help="batched mode: number of queries (0: the workload's)")
+    ap.add_argument("--query", default="0",
+                    help="query mode: comma-separated indices into the workload's queries")
     return ap.parse_args()
 
 
@@ -645,8 +650,46 @@ def run_served(args):
     }), flush=True)
 
 
+def run_query(args):
+    """Selected queries of the plain workload, one at a time: W untimed
+    rounds, then K rounds; one line with each query's mean device time."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2106_14038_b300 as gs
+    w, triples, qs = _workload(args.workload)
+    g = gs.Graph(*triples, w.n_vertices, w.n_preds)
+    sel = [int(x) for x in args.query.split(",")]
+    stream = torch.cuda.current_stream()
+    dev = {i: [] for i in sel}
+    info = {}
+    launches = 0
+    for rep in range(args.warmup + args.steps):
+        for i in sel:
+            plan = g.plan(qs[i].patterns)
+            r = g.eval(plan, stream)
+            n, k = r.info()
+            ms, nl = r.stats()
+            if rep >= args.warmup:
+                dev[i].append(ms)
+                launches += nl
+            info[i] = (qs[i].shape, n, nl)
+            r.close()
+            plan.close()
+    print(json.dumps({
+        "metric": "device ms per query", "unit": "ms", "higher_is_better": False,
+        "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+        "config": {"workload": w.name, "queries": sel},
+        "queries": [{"index": i, "shape": info[i][0], "rows": info[i][1], "launches": info[i][2],
+                     "device_ms": float(np.mean(dev[i]))} for i in sel],
+        "gpu_launches": launches,
+    }), flush=True)
+
+
 def main():
     args = _args()
+    if args.mode == "query" and args.impl == "gsmart":
+        run_query(args)
+        return
     if args.mode == "scan" and args.impl == "gsmart":
         run_scan_only(args)
         return

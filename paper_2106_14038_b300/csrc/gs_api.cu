@@ -75,6 +75,7 @@ struct gs_result {
     uint8_t* head = nullptr;  // pinned copy of the control block's head
     bool ready = false;
     int mode = 0;             // 0: grid path, 1: single-block kernel
+    int resume = 0;           // grid path: first level to build (the ones before are in the arena)
     uint32_t launches = 0;
     uint64_t rows = 0;
     uint64_t out_off = 0;
@@ -149,7 +150,7 @@ gs_status enqueue(gs_result* r) {
     GS_CUDA(cudaEventRecord(r->ev0, r->st));
     gs_status rc = r->mode == 1
         ? enqueue_small(&r->plan, exec_view(r), &r->launches, r->st)
-        : enqueue_eval(r->g, &r->plan, exec_view(r), r->work, &r->launches, r->st);
+        : enqueue_eval(r->g, &r->plan, exec_view(r), r->work, &r->launches, r->st, r->resume);
     if (rc != GS_OK) return rc;
     GS_CUDA(cudaEventRecord(r->ev1, r->st));
     // the head of the control block follows the kernels to pinned memory
@@ -174,9 +175,11 @@ gs_status wait_result(gs_result* r) {
             return GS_ETIMEOUT;
         }
         if (head.status & kStEscalate) {
-            // the single-block kernel handed the query back: run the grid path
+            // the single-block kernel handed the query back: the grid path
+            // continues from the levels it completed, in the same workspace
             r->mode = 0;
-            if (r->arena_bytes < kArenaDefault) {
+            r->resume = std::min<int>((int)head.levels_done, r->plan.n_levels);
+            if (r->resume == 0 && r->arena_bytes < kArenaDefault) {
                 r->g->alloc.put(r->arena, r->st);
                 r->arena = (uint8_t*)r->g->alloc.get(kArenaDefault, r->st);
                 if (!r->arena) { set_error("gs_eval_query: cannot allocate the workspace"); return GS_ENOMEM; }
@@ -193,7 +196,8 @@ gs_status wait_result(gs_result* r) {
             r->ready = true;
             return GS_OK;
         }
-        // workspace too small: grow it and run again
+        // workspace too small: grow it and run again from the start
+        r->resume = 0;
         uint64_t need = kCtlBytes;
         for (int l = 0; l < r->plan.n_levels; ++l) need += 8 * head.n[l] + 256;
         need += 4ull * head.rows * r->plan.n_vars;

@@ -19,7 +19,7 @@
 //                 self-loops; survivors are appended with warp-aggregated
 //                 atomics.
 // Consecutive kernels are chained with programmatic dependent launch: each
-// is scheduled while the one before it runs and waits for it on entry.
+// is scheduled while the one before it finishes and waits for it on entry.
 // A parent without candidates has no children, so dead bindings never
 // reach later levels (pre-pruning). Leaves (variables with one pattern)
 // are not materialized: k_enum_range stores their range per last-level
@@ -48,6 +48,24 @@ __global__ void k_init(ExecDev E, ConstChecks cc) {
         uint32_t lo, len;
         label_range(E.out, s, p, lo, len);
         if (!in_range(E.out, lo, len, o)) atomicOr(&c->dead, 1u);
+    }
+}
+
+// Resuming from the single-block kernel at level `from`: the counts of the
+// levels from `from` on, the totals and the status start again at zero;
+// the complete levels, `dead` and the level-0 parent count stay.
+__global__ void k_resume(ExecDev E, int from) {
+    Ctl* c = E.ctl;
+    for (int l = from + threadIdx.x; l < kMaxLevels; l += blockDim.x) {
+        c->n[l] = 0;
+        c->list_n[l] = 0;
+    }
+    if (threadIdx.x == 0) {
+        c->cand = 0;
+        c->rows = 0;
+        c->status = 0;
+        c->arrive = 0;
+        c->one = 1;
     }
 }
 
@@ -150,6 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
         }
         __syncthreads();
     }
+    chain_done();
 }
 
 // ------------------------------------------------------------------ //
@@ -202,6 +221,7 @@ __global__ void __launch_bounds__(kThreads) k_bits_write(ExecDev E, int l, Level
         }
         carry += t;
     }
+    chain_done();
 }
 
 // ------------------------------------------------------------------ //
@@ -351,6 +371,7 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
             reinterpret_cast<uint32_t*>(dst)[k] = stage[k];
         __syncthreads();
     }
+    chain_done();
 }
 
 // ------------------------------------------------------------------ //
@@ -362,21 +383,29 @@ uint64_t host_level_off(const uint64_t* n, int l) {
 }
 
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
-                       cudaStream_t st) {
+                       cudaStream_t st, int start_level) {
     const dim3 nb(g->n_blocks), th(kThreads);
     Ctl* ctl = E.ctl;
-    ConstChecks cc{};
-    cc.n = (uint32_t)(P->const_triples.size() / 3);
-    if (cc.n > kMaxPatterns) cc.n = kMaxPatterns;
-    for (uint32_t i = 0; i < 3 * cc.n; ++i) cc.t[i] = P->const_triples[i];
-    k_init<<<1, kThreads, 0, st>>>(E, cc);   // zeroes the control block's head
     uint32_t nl_launch = 1;
-    if (P->needs_scan) {
-        gs_status rc = run_scan(g, P->scan, E.bits, scan_work, st, &ctl->status);
-        if (rc != GS_OK) return rc;
-        nl_launch += 3;
+    if (start_level > 0) {
+        if (P->needs_scan || start_level > P->n_levels) {
+            set_error("internal: a resumed query must be a scan-free plan");
+            return GS_EINVAL;
+        }
+        k_resume<<<1, kThreads, 0, st>>>(E, start_level);
+    } else {
+        ConstChecks cc{};
+        cc.n = (uint32_t)(P->const_triples.size() / 3);
+        if (cc.n > kMaxPatterns) cc.n = kMaxPatterns;
+        for (uint32_t i = 0; i < 3 * cc.n; ++i) cc.t[i] = P->const_triples[i];
+        k_init<<<1, kThreads, 0, st>>>(E, cc);   // zeroes the control block's head
+        if (P->needs_scan) {
+            gs_status rc = run_scan(g, P->scan, E.bits, scan_work, st, &ctl->status);
+            if (rc != GS_OK) return rc;
+            nl_launch += 3;
+        }
     }
-    for (int l = 0; l < P->n_levels; ++l) {
+    for (int l = start_level; l < P->n_levels; ++l) {
         const LevelSpec& L = P->levels[l];
         if (L.src == kSrcList) {
             GS_CUDA(launch_chained(k_bits_count, nb, th, 0, st, E, l, L));

@@ -20,6 +20,8 @@ struct Ctl {
     uint32_t dead;                 // a pattern with two constant ends has no match
     uint32_t arrive;               // blocks of the running count kernel that are done
     uint32_t roff_shift;           // its blocks took 2^roff_shift consecutive items each
+    uint32_t levels_done;          // single-block kernel: complete levels when it handed back
+    uint32_t pad;
     uint64_t bsum[kBlocks];
     uint64_t boff[kBlocks];
 };
@@ -124,7 +126,10 @@ bool small_eligible(const gs_plan* P);
 // row / column lengths (UINT64_MAX without a constant seed).
 uint64_t first_level_bound(const gs_graph* g, const gs_plan* plan);
 gs_status enqueue_small(const gs_plan* P, const ExecDev& E, uint32_t* launches, cudaStream_t st);
+// The grid path. start_level > 0 resumes a query the single-block kernel
+// handed back, whose levels 0 .. start_level - 1 are complete in E's
+// workspace (a plan without triple scan).
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
-                       cudaStream_t st);
+                       cudaStream_t st, int start_level = 0);
 
 }  // namespace gs

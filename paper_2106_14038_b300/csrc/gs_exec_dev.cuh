@@ -118,6 +118,19 @@ __device__ __forceinline__ uint64_t upper_bound_u64(const uint64_t* a, uint64_t 
     return lo;
 }
 
+// Programmatic dependent launch. A kernel of the chain waits, before its
+// first access to memory, for the one before it to finish (a no-op for a
+// kernel launched without the attribute), and lets the next one be
+// scheduled once its block has done its main work: the next kernel's
+// blocks then hold no SM resources while this one still has work to do.
+__device__ __forceinline__ void chain_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void chain_done() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Count kernels split n items into blocks of 2^shift consecutive items (a
 // power of two: a consumer finds an item's block with a shift).
 __device__ __forceinline__ uint32_t pow2_shift(uint64_t n, uint32_t nb) {
@@ -133,6 +146,7 @@ __device__ __forceinline__ uint32_t pow2_shift(uint64_t n, uint32_t nb) {
 // another. The counter is left at zero for the next count kernel.
 __device__ __forceinline__ void arrive_and_scan(Ctl* ctl, uint64_t block_total, uint64_t* total) {
     __shared__ uint32_t last;
+    chain_done();
     if (threadIdx.x == 0) {
         ctl->bsum[blockIdx.x] = block_total;
         __threadfence();   // the sum (and the block's other writes) before the count
@@ -172,15 +186,6 @@ __device__ __forceinline__ uint64_t upper_bound_roff(const uint64_t* roff, const
         if (roff_at(roff, ctl, sh, mid) <= key) lo = mid + 1; else hi = mid;
     }
     return lo;
-}
-
-// Programmatic dependent launch: a kernel of the chain lets the next one be
-// scheduled at once and waits, before its first access to memory, for the
-// one before it to finish (a no-op for a kernel launched without the
-// attribute).
-__device__ __forceinline__ void chain_enter() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 __device__ __forceinline__ bool self_ok(const ExecDev& E, const LevelSpec& L, uint32_t x) {

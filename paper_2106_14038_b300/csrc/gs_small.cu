@@ -45,10 +45,12 @@ struct PoolOut {
 
 // Evaluates the query of record Q in workspace E with the calling block.
 // Returns 0, kStEscalate or kStOverflow; on success *off / *rows give the
-// answer's byte offset (in the pool, or in the workspace) and row count.
+// answer's byte offset (in the pool, or in the workspace) and row count;
+// *done gets the number of complete levels (all of them when it returns 0
+// or escalates at the enumeration).
 __device__ uint32_t run_query_block(const ExecDev& E, const QRec& Q, uint64_t cand_budget,
                                     uint64_t row_budget, const PoolOut* po, uint64_t* off,
-                                    uint64_t* rows) {
+                                    uint64_t* rows, int* done_out) {
     Ctl* ctl = E.ctl;
     __shared__ const uint2* lv[kMaxLevels];
     __shared__ uint64_t sh_off;
@@ -62,7 +64,8 @@ __device__ uint32_t run_query_block(const ExecDev& E, const QRec& Q, uint64_t ca
     __syncthreads();
     const bool dead = ctl->dead != 0;
     const int n_levels = Q.h->n_levels;
-    int done = 0;
+    int& done = *done_out;
+    done = 0;
     for (int l = 0; l < n_levels && !dead; ++l) {
         const LevelSpec& L = Q.lv[l];
         const uint64_t np = l == 0 ? 1 : ctl->n[l - 1];
@@ -194,11 +197,16 @@ __global__ void __launch_bounds__(kThreads) k_query_block(ExecDev E, RecParam P)
     __syncthreads();
     const QRec Q = rec_view(rec);
     uint64_t off = 0, rows = 0;
-    uint32_t st = run_query_block(E, Q, kPlainCand, kPlainRows, nullptr, &off, &rows);
+    int done = 0;
+    uint32_t st = run_query_block(E, Q, kPlainCand, kPlainRows, nullptr, &off, &rows, &done);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (st) atomicOr(&E.ctl->status, kStEscalate);
-        else E.ctl->rows = rows;
+        if (st) {
+            E.ctl->levels_done = (uint32_t)done;   // the grid path resumes here
+            atomicOr(&E.ctl->status, kStEscalate);
+        } else {
+            E.ctl->rows = rows;
+        }
     }
 }
 
@@ -224,7 +232,8 @@ __global__ void __launch_bounds__(kThreads) k_batch(BatchDev B) {
         __syncthreads();
         const QRec Q = rec_view(rec);
         uint64_t off = 0, rows = 0;
-        uint32_t st = run_query_block(E, Q, B.cand_budget, B.row_budget, &po, &off, &rows);
+        int done = 0;
+        uint32_t st = run_query_block(E, Q, B.cand_budget, B.row_budget, &po, &off, &rows, &done);
         __syncthreads();
         if (threadIdx.x == 0) {
             BatchResult r;

@@ -411,6 +411,45 @@ def test_allocation_failure_is_a_status(rmat14, fail_after):
     assert np.array_equal(g_ok.query(pats), ix.eval(pats))
 
 
+def test_handed_back_queries_resume_on_the_grid_path(rmat14, monkeypatch):
+    # constant-seeded queries past the single-block budgets: at a level
+    # (more than 1,024 candidates below a small seed level) or at the
+    # enumeration (more than 4,096 rows). The grid path continues from the
+    # levels the block finished, in its workspace; the answers equal the
+    # oracle's and the all-grid evaluation's
+    w, (s, p, o), g, ix = rmat14
+    s64, p64, o64 = (np.asarray(x, np.int64) for x in (s, p, o))
+    top = np.bincount(p64).argmax()
+    out_deg = np.bincount(s64, minlength=w.n_vertices)
+    # seeds: a constant whose top-predicate row is small, so that level 0 fits
+    seeds = [int(v) for v in np.flatnonzero((out_deg >= 20) & (out_deg <= 200))[:40]]
+    pats = []
+    for c in seeds:
+        pred = int(np.bincount(p64[s64 == c]).argmax())
+        # ?0 is a level (two patterns); ?1 a level below it; ?2 a leaf
+        pats.append([(c, pred, -1), (-1, int(top), -2), (-2, int(top), -3), (-3, int(top), -1)])
+        pats.append([(c, pred, -1), (-1, int(top), -2), (-2, int(top), -3)])
+    def run(pt):
+        r = g.eval(pt)
+        r.info()
+        nl = r.stats()[1]
+        rows = r.fetch()
+        r.close()
+        return rows, nl
+
+    resumed = 0
+    for pt in pats[:24]:
+        want = ix.eval(pt, threads=4)
+        monkeypatch.setenv("GS_EXEC", "auto")
+        got, nl = run(pt)
+        monkeypatch.setenv("GS_EXEC", "grid")
+        full, nl_full = run(pt)
+        assert np.array_equal(got, want), pt
+        assert np.array_equal(full, want), pt
+        resumed += int(1 < nl < nl_full)   # fewer launches: levels were kept
+    assert resumed >= 1
+
+
 def test_allocator_alignment_is_checked(rmat14):
     # a hook whose blocks start 16 bytes past a 256-byte boundary: the first
     # such block goes straight back to the hook and the build fails as out
