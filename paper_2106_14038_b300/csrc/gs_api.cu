@@ -128,7 +128,6 @@ void give_host_res(gs_graph* g, const cudaEvent_t ev[3], uint8_t* head) {
 
 constexpr uint64_t kArenaMin = 64ull << 20;
 constexpr uint64_t kArenaDefault = 512ull << 20;
-constexpr uint64_t kArenaSmall = 64ull << 20;   // enough for the single-block budgets
 constexpr uint64_t kSmallRoute = 8192;          // first-level bound above which a query goes straight to the grid path
 constexpr int kMaxRetries = 16;
 
@@ -438,9 +437,9 @@ gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_strea
     // budget (then it would only hand the query back)
     r->mode = (small_eligible(plan) && !force_grid && first_level_bound(g, plan) <= kSmallRoute) ? 1 : 0;
     if (rc == GS_OK) {
-        uint64_t want = kArenaSmall;
-        if (r->mode == 0)
-            want = std::max<uint64_t>(kArenaMin, std::min<uint64_t>(kArenaDefault, free_device_bytes(g) / 8));
+        // the grid path's size for both: a query the single-CTA kernel hands
+        // back continues in this workspace
+        uint64_t want = std::max<uint64_t>(kArenaMin, std::min<uint64_t>(kArenaDefault, free_device_bytes(g) / 8));
         if (const char* env = getenv("GS_ARENA_BYTES")) {   // initial workspace size
             unsigned long long v = strtoull(env, nullptr, 10);
             if (v >= 4096) want = v;

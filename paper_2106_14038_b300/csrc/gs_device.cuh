@@ -1,6 +1,7 @@
 // Device helpers shared by the kernels: searches in label-sorted rows,
-// block-wide scans and the device-wide reduce-then-scan used for every
-// count -> offset step (no kernel waits on another block).
+// block-wide scans, and the three-launch device-wide reduce-then-scan the
+// store build uses (the query path folds its count -> offset steps into the
+// count kernels instead). No kernel waits on another block.
 #pragma once
 
 #include <cuda_runtime.h>

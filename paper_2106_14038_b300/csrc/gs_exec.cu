@@ -49,6 +49,7 @@ __global__ void k_init(ExecDev E, ConstChecks cc) {
         label_range(E.out, s, p, lo, len);
         if (!in_range(E.out, lo, len, o)) atomicOr(&c->dead, 1u);
     }
+    chain_done();
 }
 
 // Resuming from the single-block kernel at level `from`: the counts of the
@@ -67,6 +68,7 @@ __global__ void k_resume(ExecDev E, int from) {
         c->arrive = 0;
         c->one = 1;
     }
+    chain_done();
 }
 
 // Candidate counts of the parent nodes of level l, as block-local
