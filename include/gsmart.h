@@ -139,7 +139,11 @@ gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint
  * (Sec. 7.2.2) and enumerated into tuples.
  *
  * gs_eval_query enqueues the work on cuda_stream and returns without
- * waiting. The result holds device memory until gs_free_result. */
+ * waiting. A plan without a full triple scan whose first level is small
+ * runs first in one CTA; if that CTA's budgets do not hold the query, the
+ * grid path continues from the levels it completed (this happens inside
+ * gs_result_info / gs_fetch_bindings, on the same stream). The result holds
+ * device memory until gs_free_result. */
 gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out);
 
 /* Number of answer rows and variables. Synchronizes the result's stream.
@@ -159,7 +163,8 @@ gs_status gs_fetch_bindings(gs_result* r, int32_t* dst, uint64_t cap_rows, int d
 
 /* Statistics of the last evaluation of r (synchronizes): device time in
  * milliseconds from CUDA events around the enqueued work, and the number of
- * kernels it launched. Either out pointer may be NULL. */
+ * kernels it launched. For a query the single CTA handed back, both cover
+ * the grid-path part only. Either out pointer may be NULL. */
 gs_status gs_result_stats(gs_result* r, float* device_ms, uint32_t* kernel_launches);
 
 /* ------------------------------------------------------------------ */
