@@ -146,11 +146,12 @@ gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint
  * device memory until gs_free_result. */
 gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out);
 
-/* Number of answer rows and variables. Synchronizes the result's stream.
+/* Number of answer rows and variables. Waits for the result's own work on
+ * its stream (work enqueued on the stream after it is not waited for).
  * When the evaluation ran out of its device workspace it is re-run with a
  * larger one; GS_ENOMEM when the device cannot hold it. The first
- * workspace is 512 MiB (at most 1/8 of free memory), or the byte count in
- * the environment variable GS_ARENA_BYTES. */
+ * workspace is 512 MiB (at most 1/8 of free memory, at least 64 MiB), or
+ * the byte count in the environment variable GS_ARENA_BYTES. */
 gs_status gs_result_info(gs_result* r, uint64_t* n_rows, uint32_t* n_vars);
 
 /* Copy the answers out: n_rows x n_vars int32, row-major, column k holds
