@@ -1,7 +1,13 @@
-"""The clock record bench.py attaches to its line: nvidia-smi CSV samples
-(index, sm, max sm, power, active reasons, hw_slowdown, hw_thermal_slowdown,
-sw_thermal_slowdown, sw_power_cap) summarised as median SM clock, maximum
-clock and the throttle reasons seen. CPU only: the samples are given."""
+"""Host-side pieces of bench.py's line, CPU only:
+- the clock record: nvidia-smi CSV samples (index, sm, max sm, power,
+  active reasons, hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown,
+  sw_power_cap) summarised as median SM clock, maximum clock and the
+  throttle reasons seen;
+- the roofline's traffic figure, reported only while the scan source is
+  the one its DRAM counters were taken on."""
+import hashlib
+import os
+
 import bench
 
 
@@ -30,3 +36,15 @@ def test_malformed_lines_are_skipped():
                   "garbage", "0, 2000, 2032, 5.0, 0x0, Not Active, Not Active, Not Active, Not Active"])
     assert s["samples"] == 1 and s["sm_mhz"] == 2000.0
     assert _summary([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_traffic_only_for_the_captured_source(monkeypatch):
+    src = os.path.join(bench.ROOT, "paper_2106_14038_b300", "csrc", "gs_scan.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    monkeypatch.setattr(bench, "SCAN_TRAFFIC", {"w": (sha[:12], 123), "old": ("0" * 12, 456),
+                                                "none": (sha[:12], None)})
+    assert bench._scan_traffic("w") == 123
+    assert bench._scan_traffic("old") is None
+    assert bench._scan_traffic("none") is None
+    assert bench._scan_traffic("unknown") is None
