@@ -309,6 +309,17 @@ gs_status gs_server_replay(gs_server* s, const gs_plan* const* plans, uint32_t n
 gs_status gs_scan_candidates(gs_graph* g, const uint32_t* preds, const uint8_t* dirs, uint32_t n,
                              uint32_t* out_bits, void* cuda_stream);
 
+/* Did the standalone scans on g complete? Synchronizes cuda_stream, then
+ * returns GS_ETIMEOUT when a bounded wait for the bulk copies of a scan
+ * enqueued by gs_scan_candidates or gs_scan_candidates_noalloc on g (on any
+ * stream, since the last call of gs_scan_status) ran out; that scan's bits
+ * are incomplete. The report is then cleared. GS_OK otherwise. Scans that
+ * gs_eval_query runs report a stall through gs_result_info instead.
+ * Allocates nothing. The wait lasts about 2 s; the environment variable
+ * GS_SCAN_STALL_CYCLES (a clock-cycle count, 0: give up at once) shortens
+ * it, for failure tests. */
+gs_status gs_scan_status(gs_graph* g, void* cuda_stream);
+
 /* gs_scan_candidates without any device allocation on the call path (the
  * paper has no counterpart; it is an engineering variant for callers that
  * must not allocate). Same arguments, result and errors as
@@ -321,7 +332,10 @@ gs_status gs_scan_candidates(gs_graph* g, const uint32_t* preds, const uint8_t* 
  *   - nothing in that array has to start at zero (each call zeroes what it
  *     accumulates into);
  *   - the first call on a device looks the array up (cudaGetSymbolAddress)
- *     and caches its address: make it before any stream capture;
+ *     and caches its address: make it before any stream capture (a first
+ *     call on a capturing stream returns GS_EINVAL);
+ *   - a stalled scan is reported by gs_scan_status, as for
+ *     gs_scan_candidates;
  *   - the current device must be the graph's (else GS_EINVAL);
  *   - all calls on one device share the array: calls whose work overlaps in
  *     time (other streams, unordered host threads) race and corrupt each

@@ -31,7 +31,7 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_server_start", "gs_server_submit", "gs_server_poll", "gs_server_fetch",
             "gs_server_release", "gs_server_stats", "gs_server_stop",
             "gs_scan_candidates_noalloc", "gs_noalloc_scratch_bytes", "gs_eval_batch_cfg",
-            "gs_batch_autotune", "gs_server_replay"]
+            "gs_batch_autotune", "gs_server_replay", "gs_scan_status"]
 
 
 class GsError(RuntimeError):
@@ -119,6 +119,7 @@ def load_library(path: str | None = None):
         "gs_result_stats": [vp, P(ctypes.c_float), P(u32)],
         "gs_scan_candidates": [vp, vp, vp, u32, vp, vp],
         "gs_scan_candidates_noalloc": [vp, vp, vp, u32, vp, vp],
+        "gs_scan_status": [vp, vp],
         "gs_eval_batch": [vp, vp, u32, vp, P(vp)],
         "gs_eval_batch_cfg": [vp, vp, u32, vp, vp, P(vp)],
         "gs_batch_autotune": [vp, vp, u32, vp, vp, P(ctypes.c_float)],
@@ -175,8 +176,10 @@ class Graph:
     def __init__(self, s, p, o, n_vertices: int, n_predicates: int, stream=None,
                  allocator: "TorchAllocator | None" = None):
         lib = load_library()
+        import torch
         self._keep = None
         self._allocator = allocator      # callbacks must outlive the graph
+        self.device = torch.cuda.current_device()
         on_dev = hasattr(s, "is_cuda") and s.is_cuda
         if on_dev:
             import torch
@@ -263,14 +266,33 @@ class Graph:
                                       ctypes.byref(cfg), ctypes.byref(ms)))
         return cfg, float(ms.value)
 
+    def _check_bits_out(self, out):
+        """The candidate-bit buffer must be a contiguous int32 CUDA tensor of
+        at least ceil(N/32) words on the graph's device (the kernel writes
+        4 * ceil(N/32) bytes into it)."""
+        import torch
+        words = (self.n_vertices + 31) // 32
+        if not isinstance(out, torch.Tensor):
+            raise ValueError("out must be a torch tensor")
+        if out.dtype != torch.int32:
+            raise ValueError("out must be int32, not %s" % out.dtype)
+        if not out.is_contiguous():
+            raise ValueError("out must be contiguous")
+        if out.numel() < words:
+            raise ValueError("out holds %d words, the vector needs %d" % (out.numel(), words))
+        if not out.is_cuda or out.device.index != self.device:
+            raise ValueError("out must be on cuda:%d, the graph's device" % self.device)
+
     def scan(self, preds, dirs, out=None, stream=None):
         """Eq. 17 / Eq. 21 on its own: a torch int32 tensor of ceil(N/32)
         words, bit x set when row x holds every preds[i] with dirs[i] == 0
-        and column x every preds[i] with dirs[i] == 1."""
+        and column x every preds[i] with dirs[i] == 1. A stalled scan is
+        reported by scan_status()."""
         import torch
         words = (self.n_vertices + 31) // 32
         if out is None:
-            out = torch.empty(words, dtype=torch.int32, device="cuda")
+            out = torch.empty(words, dtype=torch.int32, device="cuda:%d" % self.device)
+        self._check_bits_out(out)
         pr = _host_u32(preds)
         dr = np.ascontiguousarray(np.asarray(dirs), dtype=np.uint8)
         _check(_lib.gs_scan_candidates(self._h, pr.ctypes.data_as(ctypes.c_void_p),
@@ -283,9 +305,7 @@ class Graph:
         the call allocates nothing, so `out` (int32, ceil(N/32) words on the
         graph's device) is required. Calls overlapping in time on one device
         race on that array."""
-        words = (self.n_vertices + 31) // 32
-        if out.numel() < words or not out.is_cuda:
-            raise ValueError("out must be a device tensor of at least ceil(N/32) words")
+        self._check_bits_out(out)
         pr = _host_u32(preds)
         dr = np.ascontiguousarray(np.asarray(dirs), dtype=np.uint8)
         _check(_lib.gs_scan_candidates_noalloc(self._h, pr.ctypes.data_as(ctypes.c_void_p),
@@ -293,6 +313,13 @@ class Graph:
                                                ctypes.c_void_p(out.data_ptr()),
                                                _stream_handle(stream)))
         return out
+
+
+    def scan_status(self, stream=None):
+        """Synchronize the stream; raise GsError (GS_ETIMEOUT) when a bounded
+        wait of a scan()/scan_noalloc() call on this graph ran out since the
+        last check (that scan's bits are incomplete)."""
+        _check(_lib.gs_scan_status(self._h, _stream_handle(stream)))
 
 
 class Plan:

@@ -274,6 +274,11 @@ gs_status gs_load_triples(const uint32_t* s, const uint32_t* p, const uint32_t* 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     gs_status rc = build_store(g, s, p, o, n, inputs_on_device != 0, st);
     if (rc == GS_OK) {
+        g->scan_status = (uint32_t*)g->alloc.get(256, st);
+        if (!g->scan_status) { set_error("gs_load_triples: out of device memory"); rc = GS_ENOMEM; }
+        else if (cudaMemsetAsync(g->scan_status, 0, 4, st) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "gs_load_triples");
+    }
+    if (rc == GS_OK) {
         // row lengths on the host (routing estimates)
         std::vector<uint32_t> ptr((size_t)g->N + 1);
         for (int d = 0; d < 2 && rc == GS_OK; ++d) {
@@ -288,6 +293,7 @@ gs_status gs_load_triples(const uint32_t* s, const uint32_t* p, const uint32_t* 
     }
     if (rc != GS_OK) {
         free_store(g, st);
+        g->alloc.put(g->scan_status, st);
         cudaStreamSynchronize(st);
         delete g;
         return rc;
@@ -346,6 +352,32 @@ gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint
 }
 
 }  // extern "C"
+
+gs_status gs::scan_spec_from(const gs_graph* g, const uint32_t* preds, const uint8_t* dirs,
+                             uint32_t n, ScanSpec* out, const char* who) {
+    if (!g || !preds || !dirs || n == 0) { set_error("%s: NULL argument or n == 0", who); return GS_EINVAL; }
+    ScanSpec S{};
+    S.n_bvars = 1;
+    S.bvar[0] = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (preds[i] < 1 || preds[i] > g->P || dirs[i] > 1) {
+            set_error("%s: entry %u: predicate outside 1..P or direction not 0/1", who, i);
+            return GS_EINVAL;
+        }
+        uint32_t* list = dirs[i] ? S.in_pred : S.out_pred;
+        int32_t& cnt = dirs[i] ? S.n_in : S.n_out;
+        int slot = -1;
+        for (int j = 0; j < cnt; ++j) if (list[j] == preds[i]) slot = j;
+        if (slot < 0) {
+            if (cnt >= kMaxSlots) { set_error("%s: more than %d predicates in one direction", who, kMaxSlots); return GS_EINVAL; }
+            list[cnt] = preds[i];
+            slot = cnt++;
+        }
+        (dirs[i] ? S.need_in[0] : S.need_out[0]) |= 1u << slot;
+    }
+    *out = S;
+    return GS_OK;
+}
 
 // An upper bound on the candidates of the plan's first level when it is
 // seeded from constants (their row or column lengths), else UINT64_MAX.
@@ -515,35 +547,37 @@ gs_status gs_fetch_bindings(gs_result* r, int32_t* dst, uint64_t cap_rows, int d
 
 gs_status gs_scan_candidates(gs_graph* g, const uint32_t* preds, const uint8_t* dirs, uint32_t n,
                              uint32_t* out_bits, void* cuda_stream) {
-    if (!g || !preds || !dirs || !out_bits || n == 0) { set_error("gs_scan_candidates: NULL argument or n == 0"); return GS_EINVAL; }
+    if (!out_bits) { set_error("gs_scan_candidates: out_bits is NULL"); return GS_EINVAL; }
     ScanSpec S{};
-    S.n_bvars = 1;
-    S.bvar[0] = 0;
-    for (uint32_t i = 0; i < n; ++i) {
-        if (preds[i] < 1 || preds[i] > g->P || dirs[i] > 1) { set_error("gs_scan_candidates: entry %u: predicate outside 1..P or direction not 0/1", i); return GS_EINVAL; }
-        uint32_t* list = dirs[i] ? S.in_pred : S.out_pred;
-        int32_t& cnt = dirs[i] ? S.n_in : S.n_out;
-        int slot = -1;
-        for (int j = 0; j < cnt; ++j) if (list[j] == preds[i]) slot = j;
-        if (slot < 0) {
-            if (cnt >= kMaxSlots) { set_error("gs_scan_candidates: more than %d predicates in one direction", kMaxSlots); return GS_EINVAL; }
-            list[cnt] = preds[i];
-            slot = cnt++;
-        }
-        (dirs[i] ? S.need_in[0] : S.need_out[0]) |= 1u << slot;
-    }
+    gs_status rc = scan_spec_from(g, preds, dirs, n, &S, "gs_scan_candidates");
+    if (rc != GS_OK) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     void* work = g->alloc.get(scan_work_bytes(g), st);
     if (!work) { set_error("gs_scan_candidates: out of device memory"); return GS_ENOMEM; }
-    gs_status rc = run_scan(g, S, out_bits, work, st);
+    rc = run_scan(g, S, out_bits, work, st, g->scan_status);
     g->alloc.put(work, st);
     return rc;
+}
+
+gs_status gs_scan_status(gs_graph* g, void* cuda_stream) {
+    if (!g) { set_error("gs_scan_status: graph is NULL"); return GS_EINVAL; }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    uint32_t word = 0;
+    GS_CUDA(cudaMemcpyAsync(&word, g->scan_status, sizeof(word), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (!(word & kStStall)) return GS_OK;
+    GS_CUDA(cudaMemsetAsync(g->scan_status, 0, sizeof(word), st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    set_error("gs_scan_status: a bounded wait of the triple scan ran out; the candidate bits of "
+              "that scan are incomplete");
+    return GS_ETIMEOUT;
 }
 
 void gs_free_graph(gs_graph* g) {
     if (!g) return;
     cudaDeviceSynchronize();
     free_store(g, nullptr);
+    g->alloc.put(g->scan_status, nullptr);
     cudaDeviceSynchronize();
     for (int i = 0; i < g->n_side; ++i) cudaStreamDestroy(g->side[i]);
     for (cudaEvent_t e : g->ev_free) cudaEventDestroy(e);

@@ -127,6 +127,9 @@ struct gs_graph {
     std::vector<cudaEvent_t> ev_free;
     std::vector<uint8_t*> head_free;
     std::vector<uint8_t*> head_blocks;
+    // device word into which the standalone scan calls OR kStStall
+    // (read and cleared by gs_scan_status)
+    uint32_t* scan_status = nullptr;
     uint64_t free_seen = 0;   // free device memory at free_seen_at
     std::chrono::steady_clock::time_point free_seen_at{};
 };
@@ -222,11 +225,17 @@ gs_status radix_sort_u64(const gs_graph* g, uint64_t** keys, uint64_t** tmp, uin
 
 // scan.cu: candidate vectors (Eq. 17 / Eq. 21) of the variables in spec.
 // bits: spec.n_bvars vectors of ceil(N/32) words. work: scan_work_bytes().
-// status: a device word that receives kStStall if a bulk copy never
-// completes (NULL: a word inside work).
+// status: a device word into which kStStall is ORed if a bounded wait for
+// the bulk copies runs out (never cleared here).
 size_t scan_work_bytes(const gs_graph* g);
+long long scan_stall_cycles();
 gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void* work,
-                   cudaStream_t st, uint32_t* status = nullptr);
+                   cudaStream_t st, uint32_t* status);
+// The ScanSpec of one grouped selection (one candidate vector) from the
+// (predicate, direction) list of gs_scan_candidates; `who` names the entry
+// point in error messages.
+gs_status scan_spec_from(const gs_graph* g, const uint32_t* preds, const uint8_t* dirs,
+                         uint32_t n, ScanSpec* out, const char* who);
 
 // plan.cpp
 gs_status make_plan(const gs_graph* g, const int64_t* patterns, uint32_t n, uint32_t flags,

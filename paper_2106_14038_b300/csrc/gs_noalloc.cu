@@ -12,7 +12,11 @@
 //
 // Set-up: the first call on a device looks the array's address up with
 // cudaGetSymbolAddress (which may load this module) and caches it; make
-// that first call before any stream capture begins.
+// that first call before any stream capture begins (a first call on a
+// capturing stream returns GS_EINVAL).
+//
+// Stalls: a bounded wait of the scan that runs out is ORed into the graph's
+// status word (set up at load, not here) and reported by gs_scan_status.
 //
 // Races: every call on a device uses the same array. Two calls whose work
 // overlaps in time on one device (different streams, or different host
@@ -32,14 +36,24 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 std::mutex g_setup_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Address of the static array on `dev`, looked up once per device.
-gs_status scratch_for(int dev, void** out) {
+// Address of the static array on `dev`, looked up once per device. The
+// look-up may load this module, which a stream capture does not allow: a
+// first call on a capturing stream is refused.
+gs_status scratch_for(int dev, cudaStream_t st, void** out) {
     if (dev < 0 || dev >= kMaxDevices) {
         gs::set_error("gs_scan_candidates_noalloc: device %d outside 0..%d", dev, kMaxDevices - 1);
         return GS_EINVAL;
     }
     std::lock_guard<std::mutex> lk(g_setup_mu);
     if (!g_scratch_ptr[dev]) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+        if (ce != cudaSuccess) return gs::cuda_fail(ce, "cudaStreamIsCapturing");
+        if (cap != cudaStreamCaptureStatusNone) {
+            gs::set_error("gs_scan_candidates_noalloc: the first call on device %d must come "
+                          "before any stream capture (it looks up the static workspace)", dev);
+            return GS_EINVAL;
+        }
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
@@ -59,35 +73,13 @@ size_t gs_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
 
 gs_status gs_scan_candidates_noalloc(gs_graph* g, const uint32_t* preds, const uint8_t* dirs,
                                      uint32_t n, uint32_t* out_bits, void* cuda_stream) {
-    if (!g || !preds || !dirs || !out_bits || n == 0) {
-        gs::set_error("gs_scan_candidates_noalloc: NULL argument or n == 0");
+    if (!out_bits) {
+        gs::set_error("gs_scan_candidates_noalloc: out_bits is NULL");
         return GS_EINVAL;
     }
     gs::ScanSpec S{};
-    S.n_bvars = 1;
-    S.bvar[0] = 0;
-    for (uint32_t i = 0; i < n; ++i) {
-        if (preds[i] < 1 || preds[i] > g->P || dirs[i] > 1) {
-            gs::set_error("gs_scan_candidates_noalloc: entry %u: predicate outside 1..P or "
-                          "direction not 0/1", i);
-            return GS_EINVAL;
-        }
-        uint32_t* list = dirs[i] ? S.in_pred : S.out_pred;
-        int32_t& cnt = dirs[i] ? S.n_in : S.n_out;
-        int slot = -1;
-        for (int j = 0; j < cnt; ++j)
-            if (list[j] == preds[i]) slot = j;
-        if (slot < 0) {
-            if (cnt >= gs::kMaxSlots) {
-                gs::set_error("gs_scan_candidates_noalloc: more than %d predicates in one "
-                              "direction", gs::kMaxSlots);
-                return GS_EINVAL;
-            }
-            list[cnt] = preds[i];
-            slot = cnt++;
-        }
-        (dirs[i] ? S.need_in[0] : S.need_out[0]) |= 1u << slot;
-    }
+    gs_status rc = gs::scan_spec_from(g, preds, dirs, n, &S, "gs_scan_candidates_noalloc");
+    if (rc != GS_OK) return rc;
     const size_t need = gs::scan_work_bytes(g);
     if (need > kNoAllocScratchBytes) {
         gs::set_error("gs_scan_candidates_noalloc: graph needs %zu bytes of scratch (N = %u); "
@@ -103,9 +95,11 @@ gs_status gs_scan_candidates_noalloc(gs_graph* g, const uint32_t* preds, const u
         return GS_EINVAL;
     }
     void* work = nullptr;
-    gs_status rc = scratch_for(dev, &work);
+    rc = scratch_for(dev, (cudaStream_t)cuda_stream, &work);
     if (rc != GS_OK) return rc;
-    return gs::run_scan(g, S, out_bits, work, (cudaStream_t)cuda_stream);
+    // a stalled wait is reported through the graph's status word (set up
+    // when the graph was loaded), which gs_scan_status reads
+    return gs::run_scan(g, S, out_bits, work, (cudaStream_t)cuda_stream, g->scan_status);
 }
 
 }  // extern "C"

@@ -41,6 +41,8 @@
 // per vector. The streamed inputs are read with an evict-first L2 policy,
 // so the masks tend to stay in L2 until k_scan_eval reads them.
 #include <algorithm>
+#include <cstdlib>
+#include <mutex>
 
 #include "gs_device.cuh"
 
@@ -53,6 +55,7 @@ struct ScanDev {
     uint32_t out_pred[kMaxSlots];
     uint32_t in_pred[kMaxSlots];
     uint32_t n_out, n_in;
+    long long stall_cycles;   // limit of a warp's wait for its next item's copies
 };
 
 constexpr uint32_t kItemLabs = 32 * kScanLabPer;         // label slots of one item (1056)
@@ -101,11 +104,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase with parity `parity` of bar, for at most kStallCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Wait for the phase with parity `parity` of bar, for at most `limit`
+// cycles; a limit <= 0 gives up at once (failure tests).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long limit) {
+    if (limit <= 0) return false;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kStallCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
         if (lane < 2 && cn < n_items)
             nx = (ncols ? in.items : out.items)[(ncols ? cn - n0 : cn) + lane];   // in flight meanwhile
         // every lane acquires the copies itself; all lanes agree on a stall
-        const bool landed = mbar_wait_bounded(&full[warp][b], (i / kNumBuf) & 1u);
+        const bool landed = mbar_wait_bounded(&full[warp][b], (i / kNumBuf) & 1u, sd.stall_cycles);
         if (!__all_sync(0xffffffffu, landed)) { stalled = true; stall_i = i; break; }
 
         const uint4 d = desc[warp][b];
@@ -371,10 +377,12 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (stalled && lane == 0) {
         // report, then let the copies still in flight (items stall_i ..
-        // stall_i + kNumBuf - 1 of this warp) land before the warp exits
+        // stall_i + kNumBuf - 1 of this warp) land before the warp exits;
+        // this wait keeps the long limit whatever the first one was
         atomicOr(status, kStStall);
         for (uint32_t k = stall_i; k < stall_i + kNumBuf; ++k)
-            if (gw + k * GW < n_items) mbar_wait_bounded(&full[warp][k % kNumBuf], (k / kNumBuf) & 1u);
+            if (gw + k * GW < n_items)
+                mbar_wait_bounded(&full[warp][k % kNumBuf], (k / kNumBuf) & 1u, kStallCycles);
     }
 }
 
@@ -382,14 +390,12 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
 // of the item before) start at zero: the items OR their rows into them.
 __global__ void k_scan_zero(const uint2* __restrict__ items_out, uint32_t n_out,
                             const uint2* __restrict__ items_in, uint32_t n_in,
-                            uint32_t* __restrict__ mask_out, uint32_t* __restrict__ mask_in,
-                            uint32_t* __restrict__ status) {
+                            uint32_t* __restrict__ mask_out, uint32_t* __restrict__ mask_in) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // k_scan may start its copies
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     for (uint32_t c = t; c <= n_out; c += stride) mask_out[items_out[c].x >> 1] = 0;
     for (uint32_t c = t; c <= n_in; c += stride) mask_in[items_in[c].x >> 1] = 0;
-    if (t == 0 && status) *status = 0;
 }
 
 // Candidate bits: vertex v is a candidate of variable u when its row holds
@@ -427,22 +433,53 @@ __global__ void k_scan_eval(const uint16_t* __restrict__ mask_out,
 }
 
 // Workspace: mask_out | mask_in (N + 256 16-bit slots each, 16-byte
-// aligned) | status word.
+// aligned).
 static uint64_t mask_slots(uint32_t N) { return ((uint64_t)N + 256 + 7) & ~7ull; }
 
 size_t scan_work_bytes(const gs_graph* g) {
     return 4ull * mask_slots(g->N) + 512;
 }
 
+// Cycles a warp of k_scan waits for the copies of its next item before it
+// reports kStStall: about 2 s, or GS_SCAN_STALL_CYCLES when set (0: give up
+// at once), which failure tests use to make the wait run out; the warp then
+// still waits, with the long limit, for the copies it has in flight.
+long long scan_stall_cycles() {
+    if (const char* e = getenv("GS_SCAN_STALL_CYCLES")) {
+        char* end = nullptr;
+        const long long v = strtoll(e, &end, 10);
+        if (end != e && v >= 0) return v;
+    }
+    return kStallCycles;
+}
+
+// Dynamic shared memory already allowed for k_scan<LutT> on each device
+// (function attributes are per device); guarded by one mutex.
+constexpr int kAttrDevices = 64;
+static std::mutex g_attr_mu;
+static size_t g_smem_set[kAttrDevices][2];
+
+template <typename LutT>
+static gs_status allow_smem(int dev, size_t smem) {
+    if (dev < 0 || dev >= kAttrDevices) {
+        set_error("triple scan: device %d outside 0..%d", dev, kAttrDevices - 1);
+        return GS_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    size_t& set = g_smem_set[dev][sizeof(LutT) == 2 ? 1 : 0];
+    if (smem > set) {
+        GS_CUDA(cudaFuncSetAttribute(k_scan<LutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        set = smem;
+    }
+    return GS_OK;
+}
+
 template <typename LutT>
 static gs_status launch_scan(const gs_graph* g, const ScanDev& sd, uint16_t* mask_out,
                              uint16_t* mask_in, uint32_t* status, uint32_t warps, cudaStream_t st) {
     const size_t smem = scan_smem_bytes<LutT>(g->P, warps);
-    static size_t smem_set = 0;
-    if (smem > smem_set) {
-        GS_CUDA(cudaFuncSetAttribute(k_scan<LutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = smem;
-    }
+    gs_status arc = allow_smem<LutT>(g->device, smem);
+    if (arc != GS_OK) return arc;
     // one CTA per SM (the shared memory admits no second one)
     const uint32_t n_items = g->out.n_items + g->in.n_items;
     const uint32_t grid = std::max(1u, std::min((uint32_t)g->sm_count, (n_items + warps - 1) / warps));
@@ -465,16 +502,15 @@ gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void
         sd.need_out[u] = spec.need_out[u];
         sd.need_in[u] = spec.need_in[u];
     }
+    sd.stall_cycles = scan_stall_cycles();
+    if (!status) { set_error("internal: the triple scan needs a status word"); return GS_EINVAL; }
     uint16_t* mask_out = (uint16_t*)work;
     uint16_t* mask_in = mask_out + mask_slots(g->N);
-    const bool own = status == nullptr;
-    if (own) status = reinterpret_cast<uint32_t*>(mask_in + mask_slots(g->N));
     const uint32_t words = (g->N + 31) / 32;
     const int nb = g->n_blocks;
     k_scan_zero<<<nb, kThreads, 0, st>>>(g->out.items, g->out.n_items, g->in.items, g->in.n_items,
                                          reinterpret_cast<uint32_t*>(mask_out),
-                                         reinterpret_cast<uint32_t*>(mask_in),
-                                         own ? status : nullptr);
+                                         reinterpret_cast<uint32_t*>(mask_in));
     // the 16-bit one-hot table unless it costs more than a few warps
     const uint32_t w16 = scan_warps_fit(g->P, sizeof(uint16_t));
     const uint32_t w8 = scan_warps_fit(g->P, sizeof(uint8_t));

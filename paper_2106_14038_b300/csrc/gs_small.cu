@@ -13,6 +13,8 @@
 // When a level has more than the candidate budget or the answer more than
 // the row budget (or the pool is full), the query stops with kStEscalate and
 // the host re-runs it on the grid path.
+#include <mutex>
+
 #include "gs_exec_dev.cuh"
 #include "gs_qrec.h"
 
@@ -258,15 +260,25 @@ gs_status enqueue_small(const gs_plan* P, const ExecDev& E, uint32_t* launches, 
     return GS_OK;
 }
 
+// Resident k_batch CTAs per SM of the current device, looked up once per
+// device.
 int batch_blocks_per_sm() {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        int a = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch, kThreads, 0);
+    constexpr int kDevs = 64;
+    static std::mutex mu;
+    static int per_sm[kDevs] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) {
         cudaGetLastError();
-        per_sm = a > 0 ? a : 1;
+        dev = -1;
     }
-    return per_sm;
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && per_sm[dev] > 0) return per_sm[dev];
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch, kThreads, 0);
+    cudaGetLastError();
+    a = a > 0 ? a : 1;
+    if (dev >= 0) per_sm[dev] = a;
+    return a;
 }
 
 gs_status enqueue_batch(const BatchDev& B, int blocks, cudaStream_t st) {

@@ -127,3 +127,30 @@ def test_null_arguments_are_a_status_not_a_crash():
     assert lib.gs_server_poll(None, 1, None, None, None) == 1
     assert lib.gs_last_error()
     assert lib.gs_noalloc_scratch_bytes() == 48 << 20
+
+
+class _NoNative:
+    """Stands in for the loaded library: any native call fails the test."""
+
+    def __getattr__(self, name):
+        raise AssertionError("native call %s made before the argument checks" % name)
+
+
+@pytest.mark.parametrize("bad", ["dtype", "strided", "short", "host"])
+def test_scan_output_is_checked_before_any_native_call(monkeypatch, bad):
+    """scan() and scan_noalloc() write 4 * ceil(N/32) bytes into `out`: a
+    wrong dtype, a strided view, a short buffer or a host tensor is refused
+    before the library is called."""
+    import torch
+    g = gs.Graph.__new__(gs.Graph)
+    g._h, g.n_vertices, g.n_predicates, g.device = None, 100, 4, 0
+    words = 4
+    out = {"dtype": torch.zeros(words, dtype=torch.uint8),
+           "strided": torch.zeros(2 * words, dtype=torch.int32)[::2],
+           "short": torch.zeros(words - 1, dtype=torch.int32),
+           "host": torch.zeros(words, dtype=torch.int32)}[bad]
+    monkeypatch.setattr(gs, "_lib", _NoNative())
+    with pytest.raises(ValueError):
+        g.scan([1], [0], out=out)
+    with pytest.raises(ValueError):
+        g.scan_noalloc([1], [0], out)

@@ -31,8 +31,22 @@ def _heavy_graph():
     return (s, p, o), n_v, n_p
 
 
+def _oracle_bits(ix, pr, dr, n):
+    """The Eq. 17 / Eq. 21 selection from the oracle's Eq. 4 / Eq. 5 vectors."""
+    want = np.ones(n, np.uint8)
+    for q, d in zip(pr, dr):
+        want &= ix.presence(int(d), int(q))
+    return want
+
+
+def _bits(words, n):
+    w = np.asarray(words.cpu().numpy(), np.int64) & 0xffffffff
+    return ((w[:, None] >> np.arange(32)) & 1).astype(np.uint8).reshape(-1)[:n]
+
+
 def test_noalloc_matches_scan_on_consecutive_calls():
     import torch
+    import oracle
     w = rdfgen.WORKLOADS["rmat14"]
     s, p, o = rdfgen.graph(w)
     alloc = gs.TorchAllocator()
@@ -58,6 +72,14 @@ def test_noalloc_matches_scan_on_consecutive_calls():
     assert torch.cuda.memory_allocated() == used
     for (g, (pr, dr)), a, b in zip(pairs, want, outs):
         assert torch.equal(a, b), (g.n_vertices, pr, dr)
+    big.scan_status()
+    small.scan_status()
+    # the first cases also against the oracle (not only the allocating call)
+    ix_big = oracle.Index(s, p, o, w.n_vertices, w.n_preds)
+    ix_small = oracle.Index(hs, hp, ho, hn, hpn)
+    for (g, (pr, dr)), b in list(zip(pairs, outs))[:3] + list(zip(pairs, outs))[6:9]:
+        ix = ix_big if g is big else ix_small
+        assert np.array_equal(_bits(b, g.n_vertices), _oracle_bits(ix, pr, dr, g.n_vertices))
     big.close()
     small.close()
 
