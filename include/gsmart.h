@@ -107,7 +107,9 @@ gs_status gs_graph_export(const gs_graph* g, int by_column, uint32_t* ptr, uint3
  *                p is a predicate id in 1..P
  *   flags        GS_PLAN_DEGREE (Sec. 6.1.2, the default) or
  *                GS_PLAN_DIRECTION (Sec. 6.1.1; queries with constants
- *                use the degree-driven order, as the paper prescribes)
+ *                use the degree-driven order, as the paper prescribes),
+ *                optionally | GS_PLAN_LISTS (the list frontier form; a
+ *                plan that has no such form keeps candidate vectors)
  * g may be NULL: the plan is then made without a graph and its ids are
  * checked by gs_eval_query against the graph it runs on.
  * GS_EINVAL when there is no variable, the variables are not dense, an id
@@ -117,6 +119,12 @@ gs_status gs_graph_export(const gs_graph* g, int by_column, uint32_t* ptr, uint3
  * Host only. */
 #define GS_PLAN_DEGREE 0u
 #define GS_PLAN_DIRECTION 1u
+#define GS_PLAN_LISTS 2u      /* option bit: for a plan with a triple scan, only
+                                 the levels listed from the scan (roots) get a
+                                 candidate vector; later levels check the
+                                 predicates of their pending edges by a search
+                                 of each candidate's label-sorted row / column
+                                 (the pre-pruning of Sec. 7.2.2) instead */
 #define GS_MAX_PATTERNS 32
 #define GS_MAX_VARS 31
 gs_status gs_plan_query(const gs_graph* g, const int64_t* patterns, uint32_t n_patterns,
@@ -199,6 +207,19 @@ typedef struct {
                                 query to the grid path (0: 65,536) */
     uint64_t pool_bytes;     /* answer pool (0: min(4 GiB, free / 4), or
                                 GS_BATCH_POOL_BYTES) */
+    uint32_t scan_share;     /* triple scans of the plans that need one
+                                (constant-free plans): 0 or 1, shared: plans
+                                are packed into passes of at most 32
+                                predicates per direction and each pass reads
+                                the labels once (Sec. 5 grouping applied
+                                across queries); 2, one scan per plan */
+    uint32_t frontier;       /* candidate sets those plans test later levels
+                                against: 0 or 1, bitmaps (the scan writes
+                                one candidate vector per variable; a test is
+                                one bit); 2, lists (the scan writes only the
+                                vectors the plan's roots are listed from;
+                                later candidates are checked by a search of
+                                their label-sorted row or column) */
 } gs_batch_config;
 
 /* gs_eval_batch under cfg (NULL: all defaults). Grid-path queries run on
@@ -209,13 +230,23 @@ gs_status gs_eval_batch_cfg(gs_graph* g, const gs_plan* const* plans, uint32_t n
                             const gs_batch_config* cfg, void* cuda_stream, gs_batch** out);
 
 /* Autotuner: evaluates the n plans (a sample of the workload) under a fixed
- * set of candidate configurations (CTAs per SM x candidate budget x row
- * budget), each twice, and returns in *best the one with the smallest
- * wall time from enqueue to the last answer count, which goes to
- * *best_ms (may be NULL). Synchronizes cuda_stream; answers are discarded.
+ * set of candidate configurations, each twice, and returns in *best the one
+ * with the smallest wall time from enqueue to the last answer count, which
+ * goes to *best_ms (may be NULL). Stage 1 tries CTAs per SM x candidate
+ * budget x row budget; stage 2, when the sample holds plans with a triple
+ * scan, tries shared or per-plan scans x bitmap or list frontier under the
+ * stage-1 choice. The choice is kept for the life of the process, keyed by
+ * the device name, the graph's N, M and P and the sample's shape classes
+ * (scan or seeded, levels, leaves); a later call with the same key returns
+ * it without timing. Synchronizes cuda_stream; answers are discarded.
  * Every configuration gives identical answers; only time differs. */
 gs_status gs_batch_autotune(gs_graph* g, const gs_plan* const* plans, uint32_t n,
                             void* cuda_stream, gs_batch_config* best, float* best_ms);
+
+/* Triple scans the batch ran (*n_scans) and the plans they served
+ * (*n_scan_plans); with shared scans n_scans is the number of passes.
+ * Either out pointer may be NULL. Does not synchronize. */
+gs_status gs_batch_scans(gs_batch* b, uint32_t* n_scans, uint32_t* n_scan_plans);
 
 /* Non-blocking: *done = 1 once everything gs_eval_batch enqueued has
  * finished on the device (gs_batch_info then returns without waiting for the

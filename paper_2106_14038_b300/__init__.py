@@ -16,10 +16,11 @@ import numpy as np
 from ._build import LIB, build
 
 __all__ = ["Graph", "Plan", "Result", "Batch", "Server", "GsError", "TorchAllocator", "load_library", "PLAN_DEGREE",
-           "PLAN_DIRECTION", "build"]
+           "PLAN_DIRECTION", "PLAN_LISTS", "BatchConfig", "build"]
 
 PLAN_DEGREE = 0
 PLAN_DIRECTION = 1
+PLAN_LISTS = 2         # option bit: the list frontier form
 _STATUS = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOMEM", 3: "GS_ECUDA", 4: "GS_EOVERFLOW",
            5: "GS_ETIMEOUT", 6: "GS_ENOTIMPL"}
 
@@ -31,7 +32,7 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_server_start", "gs_server_submit", "gs_server_poll", "gs_server_fetch",
             "gs_server_release", "gs_server_stats", "gs_server_stop",
             "gs_scan_candidates_noalloc", "gs_noalloc_scratch_bytes", "gs_eval_batch_cfg",
-            "gs_batch_autotune", "gs_server_replay", "gs_scan_status"]
+            "gs_batch_autotune", "gs_server_replay", "gs_scan_status", "gs_batch_scans"]
 
 
 class GsError(RuntimeError):
@@ -48,7 +49,8 @@ class BatchConfig(ctypes.Structure):
     """gs_batch_config: tunables of a batched evaluation (0 = default)."""
     _fields_ = [("blocks_per_sm", ctypes.c_uint32), ("grid_streams", ctypes.c_uint32),
                 ("cand_budget", ctypes.c_uint64), ("row_budget", ctypes.c_uint64),
-                ("pool_bytes", ctypes.c_uint64)]
+                ("pool_bytes", ctypes.c_uint64), ("scan_share", ctypes.c_uint32),
+                ("frontier", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -128,6 +130,7 @@ def load_library(path: str | None = None):
         "gs_batch_fetch": [vp, u32, vp, u64, i32, i32],
         "gs_batch_stats": [vp, P(ctypes.c_float), P(u32), P(u32)],
         "gs_batch_poll": [vp, P(i32)],
+        "gs_batch_scans": [vp, P(u32), P(u32)],
         "gs_server_start": [vp, vp, P(vp)],
         "gs_server_submit": [vp, vp, P(u64)],
         "gs_server_poll": [vp, u64, P(i32), P(u64), P(ctypes.c_double)],
@@ -398,6 +401,12 @@ class Batch:
         out = np.empty((n, k), np.int32)
         _check(_lib.gs_batch_fetch(self._h, q, out.ctypes.data_as(ctypes.c_void_p), n, 0, int(sort)))
         return out
+
+    def scans(self):
+        """(triple scans run, plans they served)."""
+        a, b = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(_lib.gs_batch_scans(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
     def stats(self):
         """(device milliseconds, kernels launched, queries sent to the grid path)."""

@@ -76,6 +76,10 @@ struct gs_result {
     bool ready = false;
     int mode = 0;             // 0: grid path, 1: single-block kernel
     int resume = 0;           // grid path: first level to build (the ones before are in the arena)
+    // candidate vectors written by a triple scan shared with other queries:
+    // its completion event and status word (NULL: the query scans itself)
+    cudaEvent_t scan_ready = nullptr;
+    const uint32_t* scan_status = nullptr;
     uint32_t launches = 0;
     uint64_t rows = 0;
     uint64_t out_off = 0;
@@ -146,10 +150,12 @@ ExecDev exec_view(gs_result* r) {
 }
 
 gs_status enqueue(gs_result* r) {
+    if (r->scan_ready) GS_CUDA(cudaStreamWaitEvent(r->st, r->scan_ready, 0));
     GS_CUDA(cudaEventRecord(r->ev0, r->st));
     gs_status rc = r->mode == 1
         ? enqueue_small(&r->plan, exec_view(r), &r->launches, r->st)
-        : enqueue_eval(r->g, &r->plan, exec_view(r), r->work, &r->launches, r->st, r->resume);
+        : enqueue_eval(r->g, &r->plan, exec_view(r), r->work, &r->launches, r->st, r->resume,
+                       r->scan_status);
     if (rc != GS_OK) return rc;
     GS_CUDA(cudaEventRecord(r->ev1, r->st));
     // the head of the control block follows the kernels to pinned memory
@@ -426,8 +432,34 @@ gs_status gs::result_ready(gs_result* r, int* done) {
     return GS_OK;
 }
 
+namespace {
+
+gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
+                          uint32_t* pre_bits, cudaEvent_t pre_ready, const uint32_t* pre_status,
+                          gs_result** out);
+
+}  // namespace
+
 gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
                               gs_result** out) {
+    return eval_query_impl(g, plan, cuda_stream, force_grid, nullptr, nullptr, nullptr, out);
+}
+
+gs_status gs::eval_query_prescanned(gs_graph* g, const gs_plan* plan, void* cuda_stream,
+                                    uint32_t* bits, cudaEvent_t ready, const uint32_t* scan_status,
+                                    gs_result** out) {
+    if (!bits || !ready || !scan_status || !plan || !plan->needs_scan) {
+        set_error("internal: a prescanned query needs its vectors, event and status word");
+        return GS_EINVAL;
+    }
+    return eval_query_impl(g, plan, cuda_stream, 1, bits, ready, scan_status, out);
+}
+
+namespace {
+
+gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
+                          uint32_t* pre_bits, cudaEvent_t pre_ready, const uint32_t* pre_status,
+                          gs_result** out) {
     if (!g || !plan || !out) { set_error("gs_eval_query: NULL argument"); return GS_EINVAL; }
     *out = nullptr;
     if (plan->N == 0) {   // planned without a graph: check the ids now
@@ -443,7 +475,11 @@ gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_strea
         return GS_EINVAL;
     }
     gs_result* r = new (std::nothrow) gs_result();
-    if (!r) { set_error("gs_eval_query: host out of memory"); return GS_ENOMEM; }
+    if (!r) {
+        if (pre_bits) g->alloc.put(pre_bits, (cudaStream_t)cuda_stream);
+        set_error("gs_eval_query: host out of memory");
+        return GS_ENOMEM;
+    }
     r->g = g;
     r->plan = *plan;
     r->st = (cudaStream_t)cuda_stream;
@@ -453,7 +489,11 @@ gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_strea
     if (take_host_res(g, ev, &r->head) != GS_OK) {
         rc = GS_ECUDA;
     }
-    if (rc == GS_OK && plan->needs_scan) {
+    if (pre_bits) {   // the result owns the shared scan's vectors from here on
+        r->bits = pre_bits;
+        r->scan_ready = pre_ready;
+        r->scan_status = pre_status;
+    } else if (rc == GS_OK && plan->needs_scan) {
         r->bits = (uint32_t*)g->alloc.get(4 * words * std::max(1, plan->n_levels), r->st);
         r->work = g->alloc.get(scan_work_bytes(g), r->st);
         if (!r->bits || !r->work) { set_error("gs_eval_query: out of device memory"); rc = GS_ENOMEM; }
@@ -485,6 +525,8 @@ gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_strea
     *out = r;
     return GS_OK;
 }
+
+}  // namespace
 
 extern "C" {
 

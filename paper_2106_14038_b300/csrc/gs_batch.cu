@@ -9,9 +9,13 @@
 // side on the graph's side streams, each as an ordinary result.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "gs_device.cuh"
@@ -48,6 +52,17 @@ struct gs_batch {
     std::vector<uint32_t> todo;            // queries waiting for the grid path
     std::vector<uint32_t> active;          // queries on the grid path now
     size_t todo_next = 0;
+    // shared triple scans: the pass of each query (-1: none), the candidate
+    // vectors a pass wrote for it (owned here until its grid-path result
+    // takes them), one completion event and status word per pass
+    std::vector<int32_t> pass_of;
+    std::vector<uint32_t*> scan_bits;
+    std::vector<cudaEvent_t> ev_pass;
+    uint32_t* pass_status = nullptr;       // in dev
+    void* scan_work = nullptr;
+    std::vector<gs_plan> form;             // plans switched to the configured frontier form
+    std::vector<int32_t> form_of;          // index into form (-1: the caller's plan)
+    uint32_t n_scans = 0, n_scan_plans = 0;
 };
 
 namespace {
@@ -76,11 +91,23 @@ gs_status side_stream(gs_graph* g, uint32_t i, cudaStream_t* out) {
     return GS_OK;
 }
 
-// The grid path for plan on the batch's next side stream.
-gs_status grid_query(gs_batch* b, const gs_plan* plan, gs_result** r) {
+const gs_plan* plan_of(const gs_batch* b, uint32_t q) {
+    return b->form_of.empty() || b->form_of[q] < 0 ? b->plans[q] : &b->form[b->form_of[q]];
+}
+
+// The grid path for query q on the batch's next side stream (from the
+// vectors of its shared scan when it had one).
+gs_status grid_query(gs_batch* b, uint32_t q, gs_result** r) {
     cudaStream_t st = nullptr;
     gs_status rc = side_stream(b->g, b->next_side++ % b->cfg.grid_streams, &st);
     if (rc != GS_OK) return rc;
+    const gs_plan* plan = plan_of(b, q);
+    if (!b->pass_of.empty() && b->pass_of[q] >= 0) {
+        uint32_t* bits = b->scan_bits[q];
+        b->scan_bits[q] = nullptr;   // the result owns them from here on
+        const int ps = b->pass_of[q];
+        return eval_query_prescanned(b->g, plan, (void*)st, bits, b->ev_pass[ps], b->pass_status + ps, r);
+    }
     return eval_query_path(b->g, plan, (void*)st, 1, r);
 }
 
@@ -96,6 +123,8 @@ gs_batch_config resolve(const gs_graph* g, const gs_batch_config* c) {
     r.grid_streams = std::min(r.grid_streams, 16u);
     if (r.cand_budget == 0) r.cand_budget = kBatchCand;
     if (r.row_budget == 0) r.row_budget = kBatchRows;
+    if (r.scan_share == 0) r.scan_share = 1;
+    if (r.frontier == 0) r.frontier = 1;
     if (r.pool_bytes == 0) {
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
@@ -112,7 +141,7 @@ gs_status launch_todo(gs_batch* b) {
     while (b->active.size() < b->cfg.grid_streams && b->todo_next < b->todo.size()) {
         const uint32_t q = b->todo[b->todo_next++];
         gs_result* r = nullptr;
-        gs_status rc = grid_query(b, b->plans[q], &r);
+        gs_status rc = grid_query(b, q, &r);
         if (rc != GS_OK) return rc;
         b->sub[q] = r;
         b->active.push_back(q);
@@ -184,11 +213,51 @@ void release(gs_batch* b) {
         b->g->alloc.put(b->dev, b->st);
         b->g->alloc.put(b->slots, b->st);
         b->g->alloc.put(b->pool, b->st);
+        b->g->alloc.put(b->scan_work, b->st);
+        for (uint32_t* bits : b->scan_bits) b->g->alloc.put(bits, b->st);
     }
+    for (cudaEvent_t e : b->ev_pass) cudaEventDestroy(e);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     if (b->ev_enq) cudaEventDestroy(b->ev_enq);
     delete b;
+}
+
+// One shared triple scan: the union of its plans' predicates per direction
+// and, per plan, its vectors with their slot masks renumbered into the union.
+struct Pass {
+    std::vector<uint32_t> out_pred, in_pred;
+    std::vector<uint32_t> queries;
+};
+
+// Slot of predicate p in list (appended when absent and room is left).
+int union_slot(std::vector<uint32_t>& list, uint32_t p, bool add) {
+    for (size_t j = 0; j < list.size(); ++j)
+        if (list[j] == p) return (int)j;
+    if (!add || list.size() >= (size_t)kMaxSlotsWide) return -1;
+    list.push_back(p);
+    return (int)list.size() - 1;
+}
+
+// Does plan P fit into pass x (adding its predicates when it does)?
+bool pass_take(Pass& x, const ScanSpec& S) {
+    size_t new_out = 0, new_in = 0;
+    for (int i = 0; i < S.n_out; ++i) new_out += union_slot(x.out_pred, S.out_pred[i], false) < 0;
+    for (int i = 0; i < S.n_in; ++i) new_in += union_slot(x.in_pred, S.in_pred[i], false) < 0;
+    if (x.out_pred.size() + new_out > (size_t)kMaxSlotsWide ||
+        x.in_pred.size() + new_in > (size_t)kMaxSlotsWide)
+        return false;
+    for (int i = 0; i < S.n_out; ++i) union_slot(x.out_pred, S.out_pred[i], true);
+    for (int i = 0; i < S.n_in; ++i) union_slot(x.in_pred, S.in_pred[i], true);
+    return true;
+}
+
+// A plan's slot mask renumbered from its own slots into the pass's.
+uint32_t remap(uint32_t need, const uint32_t* own, std::vector<uint32_t>& uni) {
+    uint32_t m = 0;
+    for (int i = 0; need >> i; ++i)
+        if ((need >> i) & 1u) m |= 1u << union_slot(uni, own[i], false);
+    return m;
 }
 
 }  // namespace
@@ -229,6 +298,16 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
     b->in_kernel.assign(n, 0);
     b->res.assign(n, BatchResult{0, 0, 0, 0});
     b->sub.assign(n, nullptr);
+    // plans in the configured frontier form (a copy when it differs)
+    b->form_of.assign(n, -1);
+    for (uint32_t q = 0; q < n; ++q) {
+        const gs_plan* P = plans[q];
+        if (P->needs_scan && P->list_ok && P->list_form != (b->cfg.frontier == 2)) {
+            b->form_of[q] = (int32_t)b->form.size();
+            b->form.push_back(*P);
+        }
+    }
+    for (gs_plan& P : b->form) switch_frontier_form(&P);
     if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_enq, cudaEventDisableTiming) != cudaSuccess) {
         gs_status rc = cuda_fail(cudaGetLastError(), "cudaEventCreate");
@@ -252,8 +331,47 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
             ++n_in;
         }
     }
+    // plans that need a triple scan: packed into shared passes (in order,
+    // a new pass when the union would pass kMaxSlotsWide in a direction)
+    std::vector<Pass> passes;
+    std::vector<EvalVec> vecs;           // every pass's vectors, pass by pass
+    std::vector<uint32_t> vec_off;       // first vector of each pass
+    if (b->cfg.scan_share == 1) {
+        b->pass_of.assign(n, -1);
+        b->scan_bits.assign(n, nullptr);
+        for (uint32_t q = 0; q < n; ++q) {
+            const gs_plan* P = plan_of(b, q);
+            if (b->in_kernel[q] || !P->needs_scan) continue;
+            if (passes.empty() || !pass_take(passes.back(), P->scan)) {
+                passes.emplace_back();
+                pass_take(passes.back(), P->scan);
+            }
+            passes.back().queries.push_back(q);
+            b->pass_of[q] = (int32_t)passes.size() - 1;
+        }
+        const uint64_t words = (g->N + 31) / 32;
+        for (Pass& x : passes) {
+            vec_off.push_back((uint32_t)vecs.size());
+            for (uint32_t q : x.queries) {
+                const gs_plan* P = plan_of(b, q);
+                uint32_t* bits = (uint32_t*)g->alloc.get(4 * words * std::max(1, P->n_levels), b->st);
+                if (!bits) { set_error("gs_eval_batch: out of device memory for candidate vectors"); release(b); return GS_ENOMEM; }
+                b->scan_bits[q] = bits;
+                const ScanSpec& S = P->scan;
+                for (int u = 0; u < S.n_bvars; ++u)
+                    vecs.push_back(EvalVec{remap(S.need_out[u], S.out_pred, x.out_pred),
+                                           remap(S.need_in[u], S.in_pred, x.in_pred),
+                                           bits + (uint64_t)S.blevel[u] * words});
+            }
+        }
+        b->n_scans = (uint32_t)passes.size();
+        for (const Pass& x : passes) b->n_scan_plans += (uint32_t)x.queries.size();
+    }
+    const uint64_t n_pass = passes.size();
     const uint64_t off_bytes = 8ull * n_in, res_bytes = sizeof(BatchResult) * (uint64_t)n_in;
-    const uint64_t dev_bytes = total + off_bytes + res_bytes + 256;
+    const uint64_t ctr_bytes = 64 + ((4 * n_pass + 63) & ~63ull);   // counters | pass status words
+    const uint64_t vec_at = total + off_bytes + res_bytes + ctr_bytes;
+    const uint64_t dev_bytes = vec_at + sizeof(EvalVec) * vecs.size() + 256;
     b->staging.assign(total + off_bytes + 16, 0);
     for (uint32_t i = 0; i < n_in; ++i) pack_record(plans[b->kidx[i]], b->staging.data() + off[i]);
     std::memcpy(b->staging.data() + total, off.data(), off_bytes);
@@ -278,7 +396,11 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
         e = cudaMemcpyAsync(b->dev, b->staging.data(), total + off_bytes, cudaMemcpyHostToDevice, b->st);
     b->res_dev = (BatchResult*)(b->dev + total + off_bytes);
     uint32_t* counters = (uint32_t*)(b->dev + total + off_bytes + res_bytes);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, 64, b->st);
+    b->pass_status = counters + 16;
+    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, ctr_bytes, b->st);
+    if (e == cudaSuccess && !vecs.empty())
+        e = cudaMemcpyAsync(b->dev + vec_at, vecs.data(), sizeof(EvalVec) * vecs.size(),
+                            cudaMemcpyHostToDevice, b->st);
     if (e != cudaSuccess) rc = cuda_fail(e, "gs_eval_batch");
     if (rc == GS_OK && n_in) {
         BatchDev B{};
@@ -299,6 +421,33 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
         B.row_budget = b->cfg.row_budget;
         rc = enqueue_batch(B, blocks, b->st);
         b->launches = 1;
+    }
+    // the shared scans, one after another on the batch's stream; the
+    // queries of a pass start on the side streams once its event is reached
+    bool wide_any = false;
+    for (const Pass& x : passes)
+        wide_any |= x.out_pred.size() > (size_t)kMaxSlots || x.in_pred.size() > (size_t)kMaxSlots;
+    if (rc == GS_OK && n_pass) {
+        b->scan_work = g->alloc.get(scan_work_bytes(g, wide_any), b->st);
+        if (!b->scan_work) { set_error("gs_eval_batch: out of device memory for the triple scan"); rc = GS_ENOMEM; }
+    }
+    for (size_t i = 0; i < passes.size() && rc == GS_OK; ++i) {
+        const Pass& x = passes[i];
+        const bool wide = x.out_pred.size() > (size_t)kMaxSlots || x.in_pred.size() > (size_t)kMaxSlots;
+        rc = scan_masks(g, x.out_pred.data(), (uint32_t)x.out_pred.size(), x.in_pred.data(),
+                        (uint32_t)x.in_pred.size(), b->scan_work, b->pass_status + i, b->st);
+        if (rc != GS_OK) break;
+        EvalArgs ea{};
+        ea.n = (i + 1 < passes.size() ? vec_off[i + 1] : (uint32_t)vecs.size()) - vec_off[i];
+        ea.list = (const EvalVec*)(b->dev + vec_at) + vec_off[i];
+        rc = scan_eval(g, b->scan_work, wide, ea, b->st);
+        if (rc != GS_OK) break;
+        cudaEvent_t ev = nullptr;
+        cudaError_t e3 = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e3 == cudaSuccess) e3 = cudaEventRecord(ev, b->st);
+        if (ev) b->ev_pass.push_back(ev);
+        if (e3 != cudaSuccess) rc = cuda_fail(e3, "gs_eval_batch");
+        b->launches += 3;
     }
     // plans outside the record format go straight to the grid path, beside
     // the batch kernel
@@ -356,6 +505,16 @@ gs_status gs::batch_advance(gs_batch* b, int* done) {
 }
 
 extern "C" {
+
+gs_status gs_batch_scans(gs_batch* b, uint32_t* n_scans, uint32_t* n_scan_plans) {
+    if (!b) { set_error("gs_batch_scans: batch is NULL"); return GS_EINVAL; }
+    uint32_t own = 0;   // plans outside the shared passes run a scan each
+    for (uint32_t q = 0; q < b->n; ++q)
+        if (!b->in_kernel[q] && plan_of(b, q)->needs_scan && (b->pass_of.empty() || b->pass_of[q] < 0)) ++own;
+    if (n_scans) *n_scans = b->n_scans + own;
+    if (n_scan_plans) *n_scan_plans = b->n_scan_plans + own;
+    return GS_OK;
+}
 
 gs_status gs_batch_poll(gs_batch* b, int* done) {
     if (!b || !done) { set_error("gs_batch_poll: NULL argument"); return GS_EINVAL; }
@@ -452,9 +611,48 @@ double time_batch(gs_graph* g, const gs_plan* const* plans, uint32_t n, const gs
 
 }  // namespace
 
+namespace {
+
+// Autotuner choices kept for the life of the process, keyed by the device,
+// the graph's sizes and the sample's shape classes.
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<gs_batch_config, float>> g_tune_cache;
+
+// Shape class of a plan: scan or seeded, frontier form available, levels,
+// leaves.
+std::string tune_key(const gs_graph* g, const gs_plan* const* plans, uint32_t n) {
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, g->device);
+    cudaGetLastError();
+    std::map<std::string, uint32_t> classes;
+    for (uint32_t q = 0; q < n; ++q) {
+        const gs_plan* P = plans[q];
+        char c[64];
+        snprintf(c, sizeof(c), "%c%c%d.%d", P->needs_scan ? 'S' : 'C', P->list_ok ? 'l' : '-',
+                 P->n_levels, P->n_leaves);
+        classes[c]++;
+    }
+    std::string k = std::string(prop.name) + "|N" + std::to_string(g->N) + "|M" +
+                    std::to_string(g->M) + "|P" + std::to_string(g->P);
+    for (auto& kv : classes) k += "|" + kv.first + "x" + std::to_string(kv.second);
+    return k;
+}
+
+}  // namespace
+
 extern "C" gs_status gs_batch_autotune(gs_graph* g, const gs_plan* const* plans, uint32_t n,
                                        void* cuda_stream, gs_batch_config* best, float* best_ms) {
     if (!g || !best || (n && !plans)) { set_error("gs_batch_autotune: NULL argument"); return GS_EINVAL; }
+    const std::string key = tune_key(g, plans, n);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *best = it->second.first;
+            if (best_ms) *best_ms = it->second.second;
+            return GS_OK;
+        }
+    }
     const uint32_t fit = (uint32_t)batch_blocks_per_sm();
     std::vector<uint32_t> bps = {1u, 2u, fit};
     std::sort(bps.begin(), bps.end());
@@ -462,11 +660,30 @@ extern "C" gs_status gs_batch_autotune(gs_graph* g, const gs_plan* const* plans,
     bps.erase(std::remove_if(bps.begin(), bps.end(), [&](uint32_t x) { return x > fit; }), bps.end());
     const uint64_t cands[] = {1ull << 12, 1ull << 16};
     const uint64_t rows[] = {1ull << 12, 1ull << 16, 1ull << 20};
+    bool scans = false, lists = false;
+    for (uint32_t q = 0; q < n; ++q) {
+        scans |= plans[q]->needs_scan;
+        lists |= plans[q]->list_ok;
+    }
     gs_batch_config cfg{};
     gs_status rc = GS_OK;
     time_batch(g, plans, n, cfg, cuda_stream, &rc);   // warm-up (allocator, streams)
     if (rc != GS_OK) return rc;
     double best_t = -1.0;
+    auto consider = [&](const gs_batch_config& c) -> gs_status {
+        double t = -1.0;
+        for (int rep = 0; rep < 2; ++rep) {
+            const double x = time_batch(g, plans, n, c, cuda_stream, &rc);
+            if (rc != GS_OK) return rc;
+            if (t < 0 || x < t) t = x;
+        }
+        if (best_t < 0 || t < best_t) {
+            best_t = t;
+            *best = c;
+        }
+        return GS_OK;
+    };
+    // stage 1: CTAs per SM x candidate budget x row budget (single-CTA path)
     for (uint32_t bp : bps)
         for (uint64_t cb : cands)
             for (uint64_t rb : rows) {
@@ -474,18 +691,26 @@ extern "C" gs_status gs_batch_autotune(gs_graph* g, const gs_plan* const* plans,
                 cfg.blocks_per_sm = bp;
                 cfg.cand_budget = cb;
                 cfg.row_budget = rb;
-                double t = -1.0;
-                for (int rep = 0; rep < 2; ++rep) {
-                    const double x = time_batch(g, plans, n, cfg, cuda_stream, &rc);
-                    if (rc != GS_OK) return rc;
-                    if (t < 0 || x < t) t = x;
-                }
-                if (best_t < 0 || t < best_t) {
-                    best_t = t;
-                    *best = cfg;
-                }
+                if (consider(cfg) != GS_OK) return rc;
             }
+    // stage 2, for samples with triple scans: shared or per-plan scans x
+    // bitmap or list frontier, under the stage-1 choice
+    if (scans) {
+        const gs_batch_config base = *best;
+        for (uint32_t share : {1u, 2u})
+            for (uint32_t fr : {1u, 2u}) {
+                if (fr == 2 && !lists) continue;
+                cfg = base;
+                cfg.scan_share = share;
+                cfg.frontier = fr;
+                if (consider(cfg) != GS_OK) return rc;
+            }
+    }
     best->grid_streams = kGridStreams;
+    if (best->scan_share == 0) best->scan_share = 1;
+    if (best->frontier == 0) best->frontier = 1;
     if (best_ms) *best_ms = (float)best_t;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {*best, (float)best_t};
     return GS_OK;
 }

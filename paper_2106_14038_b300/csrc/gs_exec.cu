@@ -38,11 +38,16 @@ namespace gs {
 
 // ------------------------------------------------------------------ //
 
-__global__ void k_init(ExecDev E, ConstChecks cc) {
+// inherit: NULL, or the status word of a triple scan shared with other
+// queries, whose kStStall the query takes over.
+__global__ void k_init(ExecDev E, ConstChecks cc, const uint32_t* inherit) {
     Ctl* c = E.ctl;
     for (uint32_t i = threadIdx.x; i < kCtlHead / 8; i += blockDim.x) ((uint64_t*)c)[i] = 0;
     __syncthreads();
-    if (threadIdx.x == 0) c->one = 1;
+    if (threadIdx.x == 0) {
+        c->one = 1;
+        if (inherit) c->status = *inherit & kStStall;
+    }
     for (uint32_t i = threadIdx.x; i < cc.n; i += blockDim.x) {
         uint32_t s = cc.t[3 * i], p = cc.t[3 * i + 1], o = cc.t[3 * i + 2];
         uint32_t lo, len;
@@ -385,7 +390,7 @@ uint64_t host_level_off(const uint64_t* n, int l) {
 }
 
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
-                       cudaStream_t st, int start_level) {
+                       cudaStream_t st, int start_level, const uint32_t* scanned) {
     const dim3 nb(g->n_blocks), th(kThreads);
     Ctl* ctl = E.ctl;
     uint32_t nl_launch = 1;
@@ -400,8 +405,8 @@ gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, vo
         cc.n = (uint32_t)(P->const_triples.size() / 3);
         if (cc.n > kMaxPatterns) cc.n = kMaxPatterns;
         for (uint32_t i = 0; i < 3 * cc.n; ++i) cc.t[i] = P->const_triples[i];
-        k_init<<<1, kThreads, 0, st>>>(E, cc);   // zeroes the control block's head
-        if (P->needs_scan) {
+        k_init<<<1, kThreads, 0, st>>>(E, cc, scanned);   // zeroes the control block's head
+        if (P->needs_scan && !scanned) {
             gs_status rc = run_scan(g, P->scan, E.bits, scan_work, st, &ctl->status);
             if (rc != GS_OK) return rc;
             nl_launch += 3;

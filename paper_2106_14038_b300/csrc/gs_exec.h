@@ -128,8 +128,16 @@ uint64_t first_level_bound(const gs_graph* g, const gs_plan* plan);
 gs_status enqueue_small(const gs_plan* P, const ExecDev& E, uint32_t* launches, cudaStream_t st);
 // The grid path. start_level > 0 resumes a query the single-block kernel
 // handed back, whose levels 0 .. start_level - 1 are complete in E's
-// workspace (a plan without triple scan).
+// workspace (a plan without triple scan). scanned != NULL: the candidate
+// vectors are already in E.bits (a triple scan shared with other queries,
+// whose status word `scanned` is); the query runs no scan of its own.
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
-                       cudaStream_t st, int start_level = 0);
+                       cudaStream_t st, int start_level = 0, const uint32_t* scanned = nullptr);
+// A grid-path evaluation of a plan whose candidate vectors a shared triple
+// scan writes into `bits` (n_levels vectors of ceil(N/32) words, taken over
+// by the result); its stream waits for `ready` before the first kernel, and
+// `scan_status` is that scan's status word.
+gs_status eval_query_prescanned(gs_graph* g, const gs_plan* plan, void* cuda_stream, uint32_t* bits,
+                                cudaEvent_t ready, const uint32_t* scan_status, gs_result** out);
 
 }  // namespace gs

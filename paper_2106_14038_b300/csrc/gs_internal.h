@@ -20,7 +20,8 @@ constexpr int kMaxLevels = 32;               // one materialized level per varia
 constexpr int kMaxBinders = 8;               // edges joining a level's variable to bound ends
 constexpr int kMaxProbes = 16;               // presence tests on a level's candidates
 constexpr int kMaxSelf = 8;                  // self-loop patterns ?w p ?w per variable
-constexpr int kMaxSlots = 16;                // distinct predicates per direction in one scan
+constexpr int kMaxSlots = 16;                // distinct predicates per direction in one query's scan
+constexpr int kMaxSlotsWide = 32;            // ... in one scan shared by several queries (32-bit masks)
 constexpr int kBlocks = 1024;                // upper bound of the fixed grid (blocks)
 constexpr int kThreads = 256;
 
@@ -186,6 +187,7 @@ struct ScanSpec {
     uint32_t in_pred[kMaxSlots];
     int32_t n_bvars;                   // candidate vectors produced
     int32_t bvar[kMaxVars];            // which variable each vector belongs to
+    int32_t blevel[kMaxVars];          // its level (the vector goes to bits + level * words)
     uint32_t need_out[kMaxVars];       // slot masks that must all be present
     uint32_t need_in[kMaxVars];
 };
@@ -210,7 +212,23 @@ struct gs_plan {
     bool needs_scan = false;
     gs::ScanSpec scan{};
     std::vector<uint32_t> const_triples;   // patterns with two constant ends: s, p, o
+    // The two frontier forms of a plan with a triple scan. Bitmap form (the
+    // default): every level tests its candidates against its variable's
+    // candidate vector. List form: only the levels listed from a candidate
+    // vector (roots) get one; the others keep their predicate-presence
+    // probes (lookups in label-sorted rows). list_ok: the list form exists
+    // (no level has more probes than kMaxProbes).
+    bool list_ok = false;
+    bool list_form = false;                // levels / scan hold the list form
+    gs::LevelSpec levels_alt[gs::kMaxLevels];   // the other form's levels
+    gs::ScanSpec scan_alt{};                    // the other form's scan
 };
+
+namespace gs {
+// The plan in the other frontier form (bitmap <-> list); false when the
+// plan has no list form.
+bool switch_frontier_form(gs_plan* P);
+}  // namespace gs
 
 namespace gs {
 
@@ -227,10 +245,35 @@ gs_status radix_sort_u64(const gs_graph* g, uint64_t** keys, uint64_t** tmp, uin
 // bits: spec.n_bvars vectors of ceil(N/32) words. work: scan_work_bytes().
 // status: a device word into which kStStall is ORed if a bounded wait for
 // the bulk copies runs out (never cleared here).
-size_t scan_work_bytes(const gs_graph* g);
+// wide: 32-bit masks (up to kMaxSlotsWide predicates per direction).
+size_t scan_work_bytes(const gs_graph* g, bool wide = false);
 long long scan_stall_cycles();
 gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void* work,
                    cudaStream_t st, uint32_t* status);
+
+// One candidate vector to write: vertex x is set when its row mask holds
+// every slot of need_out and its column mask every slot of need_in.
+struct EvalVec {
+    uint32_t need_out, need_in;
+    uint32_t* dst;    // ceil(N/32) words
+};
+// The vectors of one k_scan_eval launch: list (device memory, n entries)
+// or, when list is NULL, the first n entries of inl.
+struct EvalArgs {
+    uint32_t n;
+    const EvalVec* list;
+    EvalVec inl[kMaxVars];
+};
+// The two halves of run_scan, for scans shared by several queries:
+// scan_masks streams both orientations once and leaves per-vertex masks of
+// the given predicate slots in work (32-bit masks when either direction has
+// more than kMaxSlots predicates, so work must hold scan_work_bytes(g,
+// true) then); scan_eval turns them into the vectors of ea.
+gs_status scan_masks(const gs_graph* g, const uint32_t* out_pred, uint32_t n_out,
+                     const uint32_t* in_pred, uint32_t n_in, void* work, uint32_t* status,
+                     cudaStream_t st);
+gs_status scan_eval(const gs_graph* g, const void* work, bool wide, const EvalArgs& ea,
+                    cudaStream_t st);
 // The ScanSpec of one grouped selection (one candidate vector) from the
 // (predicate, direction) list of gs_scan_candidates; `who` names the entry
 // point in error messages.

@@ -194,7 +194,7 @@ gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t 
         set_error("gs_plan_query: need 1..%d patterns", kMaxPatterns);
         return GS_EINVAL;
     }
-    if (flags > GS_PLAN_DIRECTION) { set_error("gs_plan_query: unknown flags %u", flags); return GS_EINVAL; }
+    if ((flags & ~(GS_PLAN_DIRECTION | GS_PLAN_LISTS)) != 0) { set_error("gs_plan_query: unknown flags %u", flags); return GS_EINVAL; }
     const uint32_t N = g ? g->N : 0xffffffffu, NP = g ? g->P : 65535u;
     int k = 0;
     std::vector<char> used(kMaxVars + 1, 0);
@@ -226,7 +226,7 @@ gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t 
     std::vector<int> roots;
     bool has_const = false;
     for (auto& v : G.V) has_const |= v.is_const;
-    if (flags == GS_PLAN_DIRECTION && !has_const) direction_driven(G, groups, roots);
+    if ((flags & GS_PLAN_DIRECTION) && !has_const) direction_driven(G, groups, roots);
     else degree_driven(G, groups, roots);
     for (auto& gr : groups) P->groups.push_back({G.V[gr.first].code(), gr.second});
     for (int r : roots) P->roots.push_back(G.V[r].code());
@@ -353,41 +353,61 @@ gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t 
 
     P->needs_scan = need_scan;
     if (need_scan) {
-        // candidate vectors of every materialized variable over all its patterns
-        ScanSpec& S = P->scan;
-        std::memset(&S, 0, sizeof(S));
+        // Bitmap form: candidate vectors of every materialized variable over
+        // all its patterns. List form: vectors only for the levels listed
+        // from one (roots); the other levels keep their probes.
         auto slot = [&](uint32_t* preds, int32_t& cnt, uint32_t p) -> int {
             for (int j = 0; j < cnt; ++j) if (preds[j] == p) return j;
             if (cnt >= kMaxSlots) return -1;
             preds[cnt] = p;
             return cnt++;
         };
-        for (int l = 0; l < P->n_levels; ++l) {
-            int w = order[l];
-            int bi = S.n_bvars++;
-            S.bvar[bi] = w;
-            for (uint32_t i = 0; i < n; ++i) {
-                int a = var_of(pat[3 * i]), b = var_of(pat[3 * i + 2]);
-                uint32_t p = (uint32_t)pat[3 * i + 1];
-                if (a == w) {
-                    int s = slot(S.out_pred, S.n_out, p);
-                    if (s < 0) { delete P; set_error("gs_plan_query: more than %d distinct out-predicates", kMaxSlots); return GS_ENOTIMPL; }
-                    S.need_out[bi] |= 1u << s;
-                }
-                if (b == w) {
-                    int s = slot(S.in_pred, S.n_in, p);
-                    if (s < 0) { delete P; set_error("gs_plan_query: more than %d distinct in-predicates", kMaxSlots); return GS_ENOTIMPL; }
-                    S.need_in[bi] |= 1u << s;
+        auto make_scan = [&](ScanSpec& S, bool roots_only) -> gs_status {
+            std::memset(&S, 0, sizeof(S));
+            for (int l = 0; l < P->n_levels; ++l) {
+                if (roots_only && P->levels[l].src != kSrcList) continue;
+                int w = order[l];
+                int bi = S.n_bvars++;
+                S.bvar[bi] = w;
+                S.blevel[bi] = l;
+                for (uint32_t i = 0; i < n; ++i) {
+                    int a = var_of(pat[3 * i]), b = var_of(pat[3 * i + 2]);
+                    uint32_t p = (uint32_t)pat[3 * i + 1];
+                    if (a == w) {
+                        int s = slot(S.out_pred, S.n_out, p);
+                        if (s < 0) { set_error("gs_plan_query: more than %d distinct out-predicates", kMaxSlots); return GS_ENOTIMPL; }
+                        S.need_out[bi] |= 1u << s;
+                    }
+                    if (b == w) {
+                        int s = slot(S.in_pred, S.n_in, p);
+                        if (s < 0) { set_error("gs_plan_query: more than %d distinct in-predicates", kMaxSlots); return GS_ENOTIMPL; }
+                        S.need_in[bi] |= 1u << s;
+                    }
                 }
             }
-        }
+            return GS_OK;
+        };
+        gs_status rc = make_scan(P->scan, false);
+        if (rc == GS_OK && !too_many_probes) rc = make_scan(P->scan_alt, true);
+        if (rc != GS_OK) { delete P; return rc; }
+        P->list_ok = !too_many_probes;
         for (int l = 0; l < P->n_levels; ++l) {
+            P->levels_alt[l] = P->levels[l];          // list form: the probes stay
             P->levels[l].use_bitmap = 1;
             P->levels[l].n_probes = 0;
         }
+        if ((flags & GS_PLAN_LISTS) && P->list_ok) switch_frontier_form(P);
     }
     *out = P;
     return GS_OK;
+}
+
+bool switch_frontier_form(gs_plan* P) {
+    if (!P->needs_scan || !P->list_ok) return false;
+    for (int l = 0; l < P->n_levels; ++l) std::swap(P->levels[l], P->levels_alt[l]);
+    std::swap(P->scan, P->scan_alt);
+    P->list_form = !P->list_form;
+    return true;
 }
 
 }  // namespace gs

@@ -48,12 +48,11 @@
 
 namespace gs {
 
-struct ScanDev {
-    uint32_t n_bvars;
-    uint32_t need_out[kMaxVars];
-    uint32_t need_in[kMaxVars];
-    uint32_t out_pred[kMaxSlots];
-    uint32_t in_pred[kMaxSlots];
+// The predicates k_scan tests: slot i of a direction is predicate
+// out_pred[i] (rows) / in_pred[i] (columns).
+struct ScanPreds {
+    uint32_t out_pred[kMaxSlotsWide];
+    uint32_t in_pred[kMaxSlotsWide];
     uint32_t n_out, n_in;
     long long stall_cycles;   // limit of a warp's wait for its next item's copies
 };
@@ -64,10 +63,16 @@ constexpr uint32_t kHeadCopy = 48;                       // room for an item's r
 constexpr uint32_t kBufWords = kItemLabs + 32 + kGap + kHeadCopy;   // labels | gap | starts | ptr | masks
 constexpr uint32_t kNumBuf = 2;                          // items in shared memory per warp
 constexpr uint32_t kScanWarps = 20;                      // most warps per CTA, each on its own items
-constexpr uint32_t kPmWords = kItemLabs / 2 + 32;        // 16-bit run ORs | 32 lane totals
-constexpr uint32_t kWarpWords = kNumBuf * kBufWords + kPmWords;
+// Per warp: kNumBuf item buffers, then the run ORs of one item (one mask
+// per label position) and the 32 lane totals.
+template <typename MaskT>
+__host__ __device__ constexpr uint32_t pm_words() { return kItemLabs * (uint32_t)sizeof(MaskT) / 4 + 32; }
+template <typename MaskT>
+__host__ __device__ constexpr uint32_t warp_words() { return kNumBuf * kBufWords + pm_words<MaskT>(); }
 constexpr long long kStallCycles = 4000000000LL;         // about 2 s at 2 GHz
-static_assert(kBufWords % 4 == 0 && kPmWords % 4 == 0 && kWarpWords % 4 == 0,
+static_assert(kBufWords % 4 == 0 && pm_words<uint16_t>() % 4 == 0 &&
+                  pm_words<uint32_t>() % 4 == 0 && warp_words<uint16_t>() % 4 == 0 &&
+                  warp_words<uint32_t>() % 4 == 0,
               "bulk-copy destinations must stay 16-byte aligned");
 
 // ---- bulk copies and mbarriers (inline PTX) ----
@@ -174,33 +179,31 @@ __device__ __forceinline__ void issue_item(uint32_t lane, uint32_t* buf, uint64_
 
 // label -> one-hot slot bit of this direction's query predicates
 template <typename LutT>
-__device__ __forceinline__ uint32_t lut_bit(const LutT* lut, uint32_t l);
-template <>
-__device__ __forceinline__ uint32_t lut_bit<uint16_t>(const uint16_t* lut, uint32_t l) {
-    return lut[l];
-}
-template <>
-__device__ __forceinline__ uint32_t lut_bit<uint8_t>(const uint8_t* lut, uint32_t l) {
-    return (1u << lut[l]) >> 1;   // the byte table holds slot + 1 (0: none)
+__device__ __forceinline__ uint32_t lut_bit(const LutT* lut, uint32_t l) {
+    if constexpr (sizeof(LutT) == 1)
+        return (uint32_t)((1ull << lut[l]) >> 1);   // the byte table holds slot + 1 (0: none)
+    else
+        return lut[l];                              // one-hot already
 }
 
-__device__ __forceinline__ uint32_t eval_bits(const ScanDev& sd, uint32_t mo, uint32_t mi,
-                                              uint32_t u) {
-    return ((mo & sd.need_out[u]) == sd.need_out[u]) && ((mi & sd.need_in[u]) == sd.need_in[u]);
+__device__ __forceinline__ uint32_t eval_bit(const EvalVec& v, uint32_t mo, uint32_t mi) {
+    return ((mo & v.need_out) == v.need_out) && ((mi & v.need_in) == v.need_in);
 }
 
-// Dynamic shared memory: per warp kNumBuf buffers | pm | head words; then the lut.
-template <typename LutT>
+// Dynamic shared memory: per warp kNumBuf buffers | run ORs | lane totals;
+// then the two luts.
+template <typename LutT, typename MaskT>
 size_t scan_smem_bytes(uint32_t P, uint32_t warps) {
-    return 4ull * warps * kWarpWords + 2 * sizeof(LutT) * ((size_t)P + 2);
+    return 4ull * warps * warp_words<MaskT>() + 2 * sizeof(LutT) * ((size_t)P + 2);
 }
 
 // Warps per CTA that fit beside two luts of P + 2 entries of lut_bytes each.
+template <typename MaskT>
 static uint32_t scan_warps_fit(uint32_t P, size_t lut_bytes) {
     const size_t avail = 227u * 1024u - 1536u;   // less the static shared memory
     const size_t lut = 2 * lut_bytes * ((size_t)P + 2);
     if (lut >= avail) return 0;
-    return (uint32_t)std::min<size_t>(kScanWarps, (avail - lut) / (4ull * kWarpWords));
+    return (uint32_t)std::min<size_t>(kScanWarps, (avail - lut) / (4ull * warp_words<MaskT>()));
 }
 
 // One orientation of the matrix as the scan sees it.
@@ -209,7 +212,7 @@ struct ScanSide {
     const uint32_t* heads;
     const uint2* items;
     uint32_t n_items;
-    uint16_t* mask;   // per vertex: the query predicates of this direction its row holds
+    void* mask;   // per vertex (MaskT): the query predicates of this direction its row holds
 };
 
 // Both orientations in one grid: items 0 .. out.n_items - 1 are the CSR's,
@@ -217,16 +220,17 @@ struct ScanSide {
 // over all warps of the grid) with its own buffers; it syncs only with
 // itself. Launched dependent on k_scan_zero: the first copies are issued
 // before waiting for it, the masks are written after.
-template <typename LutT>
+template <typename LutT, typename MaskT>
 __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanSide in, uint32_t N,
-                                                             uint32_t P, ScanDev sd,
+                                                             uint32_t P, ScanPreds sd,
                                                              uint32_t* status) {
     extern __shared__ __align__(128) uint32_t dsm[];
+    constexpr uint32_t kWarpWords = warp_words<MaskT>();
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const uint32_t n_warps = blockDim.x >> 5;
     uint32_t* bufs = dsm + warp * kWarpWords;
-    uint16_t* pm = (uint16_t*)(bufs + kNumBuf * kBufWords);   // pm[p]: run OR at position p
-    uint32_t* cont = bufs + kNumBuf * kBufWords + kItemLabs / 2;   // cont[l]: lane l's run total
+    MaskT* pm = (MaskT*)(bufs + kNumBuf * kBufWords);   // pm[p]: run OR at position p
+    uint32_t* cont = bufs + kNumBuf * kBufWords + kItemLabs * (uint32_t)sizeof(MaskT) / 4;   // cont[l]: lane l's run total
     LutT* luts = (LutT*)(dsm + n_warps * kWarpWords);   // out-predicates | in-predicates
     __shared__ __align__(8) uint64_t full[kScanWarps][kNumBuf];
     __shared__ uint4 desc[kScanWarps][kNumBuf];
@@ -241,10 +245,10 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
     __syncthreads();
     if (threadIdx.x < sd.n_out)
         luts[sd.out_pred[threadIdx.x]] =
-            sizeof(LutT) == 2 ? (LutT)(1u << threadIdx.x) : (LutT)(threadIdx.x + 1);
+            sizeof(LutT) >= 2 ? (LutT)(1u << threadIdx.x) : (LutT)(threadIdx.x + 1);
     if (threadIdx.x < sd.n_in)
         luts[P + 2 + sd.in_pred[threadIdx.x]] =
-            sizeof(LutT) == 2 ? (LutT)(1u << threadIdx.x) : (LutT)(threadIdx.x + 1);
+            sizeof(LutT) >= 2 ? (LutT)(1u << threadIdx.x) : (LutT)(threadIdx.x + 1);
     __syncthreads();
 
     const uint32_t gw = blockIdx.x * n_warps + warp;
@@ -283,7 +287,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
         const uint4 d = desc[warp][b];
         const uint32_t cols = side_of[warp][b];
         const LutT* lut = luts + (cols ? P + 2 : 0u);
-        uint16_t* mask = cols ? in.mask : out.mask;
+        MaskT* mask = (MaskT*)(cols ? in.mask : out.mask);
         const uint32_t r0 = d.x, k0 = d.y, r1 = d.z, k1 = d.w;
         const ItemLayout L = item_layout(d);
         const uint32_t* buf = bufs + b * kBufWords;
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
             for (uint32_t q = 0; q < kScanLabPer; ++q) {
                 const uint32_t keep = (uint32_t)((h64 >> q) & 1ull) - 1u;   // 0 at a head
                 acc = (acc & keep) | v[q];
-                pm[base + q] = (uint16_t)acc;
+                pm[base + q] = (MaskT)acc;
             }
             has_head = (h64 & ((1ull << kScanLabPer) - 1)) != 0;
         }
@@ -353,10 +357,18 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
             // rows sharing a 32-bit word with r0 or r1 (zeroed by
             // k_scan_zero) may be written by two items: ORed in whole words;
             // every other row lies in this item alone
-            if ((r >> 1) == (r0 >> 1) || (r >> 1) == (r1 >> 1)) {
-                if (m) atomicOr(reinterpret_cast<uint32_t*>(mask) + (r >> 1), m << (16 * (r & 1u)));
+            if constexpr (sizeof(MaskT) == 2) {
+                if ((r >> 1) == (r0 >> 1) || (r >> 1) == (r1 >> 1)) {
+                    if (m) atomicOr(reinterpret_cast<uint32_t*>(mask) + (r >> 1), m << (16 * (r & 1u)));
+                } else {
+                    mask[r] = (MaskT)m;
+                }
             } else {
-                mask[r] = (uint16_t)m;
+                if (r == r0 || r == r1) {
+                    if (m) atomicOr(reinterpret_cast<uint32_t*>(mask) + r, m);
+                } else {
+                    mask[r] = (MaskT)m;
+                }
             }
         }
         __syncwarp();   // buffer b and pm are free again
@@ -388,56 +400,70 @@ __global__ void __launch_bounds__(kScanWarps * 32, 1) k_scan(ScanSide out, ScanS
 
 // The 32-bit mask words holding an item's first row (so also the last row
 // of the item before) start at zero: the items OR their rows into them.
+// shift: 1 for 16-bit masks (two rows per word), 0 for 32-bit masks.
 __global__ void k_scan_zero(const uint2* __restrict__ items_out, uint32_t n_out,
                             const uint2* __restrict__ items_in, uint32_t n_in,
-                            uint32_t* __restrict__ mask_out, uint32_t* __restrict__ mask_in) {
+                            uint32_t* __restrict__ mask_out, uint32_t* __restrict__ mask_in,
+                            uint32_t shift) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // k_scan may start its copies
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    for (uint32_t c = t; c <= n_out; c += stride) mask_out[items_out[c].x >> 1] = 0;
-    for (uint32_t c = t; c <= n_in; c += stride) mask_in[items_in[c].x >> 1] = 0;
+    for (uint32_t c = t; c <= n_out; c += stride) mask_out[items_out[c].x >> shift] = 0;
+    for (uint32_t c = t; c <= n_in; c += stride) mask_in[items_in[c].x >> shift] = 0;
 }
 
-// Candidate bits: vertex v is a candidate of variable u when its row holds
-// every out-predicate and its column every in-predicate u needs (Eq. 21).
-// A warp takes 256 vertices at a time, eight per lane (16-byte loads of
-// both 16-bit masks); the bytes of 4 lanes are ORed into one word.
-__global__ void k_scan_eval(const uint16_t* __restrict__ mask_out,
-                            const uint16_t* __restrict__ mask_in, uint32_t N, ScanDev sd,
-                            uint32_t* __restrict__ bits, uint32_t words) {
+// Candidate bits: vertex v is in vector j when its row holds every
+// out-predicate and its column every in-predicate the vector needs
+// (Eq. 21). A warp takes 256 vertices at a time, eight per lane (16-byte
+// loads of both masks: one each for 16-bit masks, two for 32-bit ones);
+// the bytes of 4 lanes are ORed into one word of each vector.
+template <typename MaskT>
+__global__ void k_scan_eval(const MaskT* __restrict__ mask_out, const MaskT* __restrict__ mask_in,
+                            uint32_t N, EvalArgs ea, uint32_t words) {
     asm volatile("griddepcontrol.wait;" ::: "memory");   // the masks of k_scan
     const uint32_t lane = lane_id();
     const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    constexpr uint32_t kLoads = sizeof(MaskT) / 2;   // 16-byte loads per mask per lane
     for (uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g * 256 < N; g += warps) {
-        const uint32_t v = g * 256 + lane * 8;   // masks hold N + 256 slots: the load stays inside
-        const uint4 mo4 = __ldcs(reinterpret_cast<const uint4*>(mask_out + v));
-        const uint4 mi4 = __ldcs(reinterpret_cast<const uint4*>(mask_in + v));
-        const uint32_t mo[4] = {mo4.x, mo4.y, mo4.z, mo4.w};
-        const uint32_t mi[4] = {mi4.x, mi4.y, mi4.z, mi4.w};
-        for (uint32_t u = 0; u < sd.n_bvars; ++u) {
+        const uint32_t v = g * 256 + lane * 8;   // masks hold N + 256 slots: the loads stay inside
+        uint32_t mo[8], mi[8];
+#pragma unroll
+        for (uint32_t h = 0; h < kLoads; ++h) {
+            const uint4 a = __ldcs(reinterpret_cast<const uint4*>(mask_out + v) + h);
+            const uint4 b = __ldcs(reinterpret_cast<const uint4*>(mask_in + v) + h);
+            const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                if constexpr (sizeof(MaskT) == 2) {   // word k: vertices v + 2k (low), v + 2k + 1
+                    mo[2 * k] = aw[k] & 0xffffu; mo[2 * k + 1] = aw[k] >> 16;
+                    mi[2 * k] = bw[k] & 0xffffu; mi[2 * k + 1] = bw[k] >> 16;
+                } else {                              // word k of load h: vertex v + 4h + k
+                    mo[4 * h + k] = aw[k];
+                    mi[4 * h + k] = bw[k];
+                }
+            }
+        }
+        for (uint32_t j = 0; j < ea.n; ++j) {
+            const EvalVec e = ea.list ? ea.list[j] : ea.inl[j];
             uint32_t byte = 0;
 #pragma unroll
-            for (uint32_t j = 0; j < 4; ++j) {   // vertices v + 2j (low half), v + 2j + 1 (high)
-                byte |= (uint32_t)(eval_bits(sd, mo[j] & 0xffffu, mi[j] & 0xffffu, u) &&
-                                   v + 2 * j < N) << (2 * j);
-                byte |= (uint32_t)(eval_bits(sd, mo[j] >> 16, mi[j] >> 16, u) &&
-                                   v + 2 * j + 1 < N) << (2 * j + 1);
-            }
+            for (uint32_t k = 0; k < 8; ++k)
+                byte |= (uint32_t)(eval_bit(e, mo[k], mi[k]) && v + k < N) << k;
             uint32_t word = byte << (8 * (lane & 3));
             word |= __shfl_xor_sync(0xffffffffu, word, 1);
             word |= __shfl_xor_sync(0xffffffffu, word, 2);
             const uint32_t wi = g * 8 + (lane >> 2);
-            if ((lane & 3) == 0 && wi < words) bits[(uint64_t)u * words + wi] = word;
+            if ((lane & 3) == 0 && wi < words) e.dst[wi] = word;
         }
     }
 }
 
-// Workspace: mask_out | mask_in (N + 256 16-bit slots each, 16-byte
-// aligned).
+// Workspace: mask_out | mask_in (N + 256 slots of 16 or 32 bits each,
+// 16-byte aligned).
 static uint64_t mask_slots(uint32_t N) { return ((uint64_t)N + 256 + 7) & ~7ull; }
 
-size_t scan_work_bytes(const gs_graph* g) {
-    return 4ull * mask_slots(g->N) + 512;
+size_t scan_work_bytes(const gs_graph* g, bool wide) {
+    return (wide ? 8ull : 4ull) * mask_slots(g->N) + 512;
 }
 
 // Cycles a warp of k_scan waits for the copies of its next item before it
@@ -453,79 +479,110 @@ long long scan_stall_cycles() {
     return kStallCycles;
 }
 
-// Dynamic shared memory already allowed for k_scan<LutT> on each device
-// (function attributes are per device); guarded by one mutex.
+// Dynamic shared memory already allowed for each k_scan variant on each
+// device (function attributes are per device); guarded by one mutex.
 constexpr int kAttrDevices = 64;
 static std::mutex g_attr_mu;
-static size_t g_smem_set[kAttrDevices][2];
+static size_t g_smem_set[kAttrDevices][4];
 
-template <typename LutT>
+template <typename LutT, typename MaskT>
 static gs_status allow_smem(int dev, size_t smem) {
     if (dev < 0 || dev >= kAttrDevices) {
         set_error("triple scan: device %d outside 0..%d", dev, kAttrDevices - 1);
         return GS_EINVAL;
     }
+    const int variant = (sizeof(LutT) == 1 ? 0 : 1) + (sizeof(MaskT) == 2 ? 0 : 2);
     std::lock_guard<std::mutex> lk(g_attr_mu);
-    size_t& set = g_smem_set[dev][sizeof(LutT) == 2 ? 1 : 0];
+    size_t& set = g_smem_set[dev][variant];
     if (smem > set) {
-        GS_CUDA(cudaFuncSetAttribute(k_scan<LutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GS_CUDA(cudaFuncSetAttribute(k_scan<LutT, MaskT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
         set = smem;
     }
     return GS_OK;
 }
 
-template <typename LutT>
-static gs_status launch_scan(const gs_graph* g, const ScanDev& sd, uint16_t* mask_out,
-                             uint16_t* mask_in, uint32_t* status, uint32_t warps, cudaStream_t st) {
-    const size_t smem = scan_smem_bytes<LutT>(g->P, warps);
-    gs_status arc = allow_smem<LutT>(g->device, smem);
+template <typename LutT, typename MaskT>
+static gs_status launch_scan(const gs_graph* g, const ScanPreds& sd, void* mask_out, void* mask_in,
+                             uint32_t* status, uint32_t warps, cudaStream_t st) {
+    const size_t smem = scan_smem_bytes<LutT, MaskT>(g->P, warps);
+    gs_status arc = allow_smem<LutT, MaskT>(g->device, smem);
     if (arc != GS_OK) return arc;
     // one CTA per SM (the shared memory admits no second one)
     const uint32_t n_items = g->out.n_items + g->in.n_items;
     const uint32_t grid = std::max(1u, std::min((uint32_t)g->sm_count, (n_items + warps - 1) / warps));
     const ScanSide out{dview(g->out), g->out.heads, g->out.items, g->out.n_items, mask_out};
     const ScanSide in{dview(g->in), g->in.heads, g->in.items, g->in.n_items, mask_in};
-    GS_CUDA(launch_chained(k_scan<LutT>, dim3(grid), dim3(warps * 32), smem, st, out, in, g->N,
-                             g->P, sd, status));
+    GS_CUDA(launch_chained(k_scan<LutT, MaskT>, dim3(grid), dim3(warps * 32), smem, st, out, in,
+                           g->N, g->P, sd, status));
+    return GS_OK;
+}
+
+template <typename MaskT>
+static gs_status scan_masks_as(const gs_graph* g, const ScanPreds& sd, void* work, uint32_t* status,
+                               cudaStream_t st) {
+    MaskT* mask_out = (MaskT*)work;
+    MaskT* mask_in = mask_out + mask_slots(g->N);
+    k_scan_zero<<<g->n_blocks, kThreads, 0, st>>>(g->out.items, g->out.n_items, g->in.items,
+                                                  g->in.n_items, reinterpret_cast<uint32_t*>(mask_out),
+                                                  reinterpret_cast<uint32_t*>(mask_in),
+                                                  sizeof(MaskT) == 2 ? 1u : 0u);
+    // the one-hot table unless it costs more than a few warps; else the
+    // byte table (slot + 1)
+    using Wide = typename std::conditional<sizeof(MaskT) == 2, uint16_t, uint32_t>::type;
+    const uint32_t ww = scan_warps_fit<MaskT>(g->P, sizeof(Wide));
+    const uint32_t w8 = scan_warps_fit<MaskT>(g->P, sizeof(uint8_t));
+    if (ww >= 12 || ww >= w8) return launch_scan<Wide, MaskT>(g, sd, mask_out, mask_in, status, ww, st);
+    return launch_scan<uint8_t, MaskT>(g, sd, mask_out, mask_in, status, w8, st);
+}
+
+gs_status scan_masks(const gs_graph* g, const uint32_t* out_pred, uint32_t n_out,
+                     const uint32_t* in_pred, uint32_t n_in, void* work, uint32_t* status,
+                     cudaStream_t st) {
+    if (!status) { set_error("internal: the triple scan needs a status word"); return GS_EINVAL; }
+    if (n_out > (uint32_t)kMaxSlotsWide || n_in > (uint32_t)kMaxSlotsWide) {
+        set_error("internal: more than %d predicates per direction in one scan", kMaxSlotsWide);
+        return GS_EINVAL;
+    }
+    ScanPreds sd{};
+    sd.n_out = n_out;
+    sd.n_in = n_in;
+    for (uint32_t i = 0; i < n_out; ++i) sd.out_pred[i] = out_pred[i];
+    for (uint32_t i = 0; i < n_in; ++i) sd.in_pred[i] = in_pred[i];
+    sd.stall_cycles = scan_stall_cycles();
+    const bool wide = n_out > (uint32_t)kMaxSlots || n_in > (uint32_t)kMaxSlots;
+    return wide ? scan_masks_as<uint32_t>(g, sd, work, status, st)
+                : scan_masks_as<uint16_t>(g, sd, work, status, st);
+}
+
+gs_status scan_eval(const gs_graph* g, const void* work, bool wide, const EvalArgs& ea,
+                    cudaStream_t st) {
+    const uint32_t words = (g->N + 31) / 32;
+    const uint32_t eb = std::min<uint32_t>((words + 63) / 64, (uint32_t)g->sm_count * 8);
+    if (wide) {
+        const uint32_t* mo = (const uint32_t*)work;
+        GS_CUDA(launch_chained(k_scan_eval<uint32_t>, dim3(std::max(1u, eb)), dim3(kThreads), 0, st,
+                               mo, mo + mask_slots(g->N), g->N, ea, words));
+    } else {
+        const uint16_t* mo = (const uint16_t*)work;
+        GS_CUDA(launch_chained(k_scan_eval<uint16_t>, dim3(std::max(1u, eb)), dim3(kThreads), 0, st,
+                               mo, mo + mask_slots(g->N), g->N, ea, words));
+    }
+    GS_CUDA(cudaGetLastError());
     return GS_OK;
 }
 
 gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void* work,
                    cudaStream_t st, uint32_t* status) {
-    ScanDev sd{};
-    sd.n_bvars = spec.n_bvars;
-    sd.n_out = spec.n_out;
-    sd.n_in = spec.n_in;
-    for (int i = 0; i < spec.n_out; ++i) sd.out_pred[i] = spec.out_pred[i];
-    for (int i = 0; i < spec.n_in; ++i) sd.in_pred[i] = spec.in_pred[i];
-    for (int u = 0; u < spec.n_bvars; ++u) {
-        sd.need_out[u] = spec.need_out[u];
-        sd.need_in[u] = spec.need_in[u];
-    }
-    sd.stall_cycles = scan_stall_cycles();
-    if (!status) { set_error("internal: the triple scan needs a status word"); return GS_EINVAL; }
-    uint16_t* mask_out = (uint16_t*)work;
-    uint16_t* mask_in = mask_out + mask_slots(g->N);
-    const uint32_t words = (g->N + 31) / 32;
-    const int nb = g->n_blocks;
-    k_scan_zero<<<nb, kThreads, 0, st>>>(g->out.items, g->out.n_items, g->in.items, g->in.n_items,
-                                         reinterpret_cast<uint32_t*>(mask_out),
-                                         reinterpret_cast<uint32_t*>(mask_in));
-    // the 16-bit one-hot table unless it costs more than a few warps
-    const uint32_t w16 = scan_warps_fit(g->P, sizeof(uint16_t));
-    const uint32_t w8 = scan_warps_fit(g->P, sizeof(uint8_t));
-    gs_status rc;
-    if (w16 >= 12 || w16 >= w8)
-        rc = launch_scan<uint16_t>(g, sd, mask_out, mask_in, status, w16, st);
-    else
-        rc = launch_scan<uint8_t>(g, sd, mask_out, mask_in, status, w8, st);
+    gs_status rc = scan_masks(g, spec.out_pred, (uint32_t)spec.n_out, spec.in_pred,
+                              (uint32_t)spec.n_in, work, status, st);
     if (rc != GS_OK) return rc;
-    const uint32_t eb = std::min<uint32_t>((words + 63) / 64, (uint32_t)g->sm_count * 8);
-    GS_CUDA(launch_chained(k_scan_eval, dim3(std::max(1u, eb)), dim3(kThreads), 0, st,
-                             (const uint16_t*)mask_out, (const uint16_t*)mask_in, g->N, sd, bits,
-                             words));
-    GS_CUDA(cudaGetLastError());
-    return GS_OK;
+    EvalArgs ea{};
+    ea.n = (uint32_t)spec.n_bvars;
+    const uint64_t words = (g->N + 31) / 32;
+    for (int u = 0; u < spec.n_bvars; ++u)
+        ea.inl[u] = EvalVec{spec.need_out[u], spec.need_in[u], bits + (uint64_t)spec.blevel[u] * words};
+    return scan_eval(g, work, false, ea, st);
 }
 
 }  // namespace gs

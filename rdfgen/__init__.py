@@ -56,7 +56,7 @@ def _L():
         lib.rdfgen_adj_free.restype = None
         lib.rdfgen_adj_free.argtypes = [vp]
         lib.rdfgen_embed.restype = i32
-        lib.rdfgen_embed.argtypes = [vp, u32, u32, vp, vp, vp, u64, u64, vp, vp, vp]
+        lib.rdfgen_embed.argtypes = [vp, u32, u32, vp, vp, vp, vp, vp, u64, u64, vp, vp, vp]
         lib.rdfgen_tree_bound.restype = dbl
         lib.rdfgen_tree_bound.argtypes = [vp, u32, vp, vp, vp, vp, vp]
         lib.rdfgen_tree_bound_rooted.restype = dbl
@@ -102,6 +102,7 @@ class Shape:
     n_tree: int            # = n_v - 1
     const: list = field(default_factory=list)     # shape vertices that are constants
     dir_req: dict = field(default_factory=dict)   # edge index -> 1 (u subject) / 2 (u object)
+    pred_range: dict = field(default_factory=dict)  # edge index -> (lowest, highest) predicate id
 
 
 def star(k: int) -> Shape:
@@ -128,6 +129,13 @@ def snowflake(branches) -> Shape:
     return Shape("snowflake%d" % nxt, nxt, edges, nxt - 1)
 
 
+def cycle_leaf(k: int) -> Shape:
+    """A k-cycle 0-1-..-(k-1)-0 with one pendant vertex k on vertex 0: the
+    tree edges (the path and the pendant edge) first, the closing edge last."""
+    e = [(i, i + 1) for i in range(k - 1)] + [(0, k), (k - 1, 0)]
+    return Shape("cycle%d+leaf" % k, k + 1, e, k)
+
+
 @dataclass
 class Query:
     patterns: np.ndarray   # (n, 3) int64: s, p, o; variable k is -(k+1)
@@ -135,6 +143,7 @@ class Query:
     shape: str
     bound: float           # matches of the spanning tree (upper bound on the result)
     embedding: np.ndarray  # graph vertex of every shape vertex (one known match)
+    u_subject: np.ndarray = None   # per shape edge: 1 when its first end is the subject
 
 
 class Sampler:
@@ -176,10 +185,21 @@ class Sampler:
         pat = np.zeros((len(shape.edges), 3), np.int64)
         mapped = np.zeros(shape.n_v, np.uint32)
         usub = np.zeros(len(shape.edges), np.uint8)
+        plo = phi = None
+        if shape.pred_range:
+            plo = np.ones(len(shape.edges), np.uint32)
+            phi = np.full(len(shape.edges), self.n_preds, np.uint32)
+            for e, (lo, hi) in shape.pred_range.items():
+                plo[e], phi[e] = lo, hi
         rc = _L().rdfgen_embed(self._h, shape.n_v, len(shape.edges), _ptr(se), _ptr(isc),
-                               _ptr(dreq), seed, attempt, _ptr(pat), _ptr(mapped), _ptr(usub))
+                               _ptr(dreq), None if plo is None else _ptr(plo),
+                               None if phi is None else _ptr(phi), seed, attempt, _ptr(pat),
+                               _ptr(mapped), _ptr(usub))
         if rc != 0:
             return None
+        if not with_bound:
+            return Query(pat, shape.n_v - len(shape.const), shape.name, float("nan"), mapped,
+                         usub)
         bound = float("nan")
         if with_bound and work_cap > 0 and shape.const:
             bound = _L().rdfgen_tree_bound_rooted(self._h, shape.n_v, _ptr(se), _ptr(isc),
@@ -190,7 +210,17 @@ class Sampler:
         elif with_bound:
             bound = _L().rdfgen_tree_bound(self._h, shape.n_v, _ptr(se), _ptr(isc), _ptr(mapped),
                                            _ptr(pat), _ptr(usub))
-        return Query(pat, shape.n_v - len(shape.const), shape.name, bound, mapped)
+        return Query(pat, shape.n_v - len(shape.const), shape.name, bound, mapped, usub)
+
+    def tree_bound(self, shape: Shape, q: Query) -> float:
+        """Match count of the shape's spanning tree (its first n_v - 1 edges)
+        under q's predicates and directions: an upper bound on q's answers."""
+        se = np.array(shape.edges, np.uint32).reshape(-1)
+        isc = np.zeros(shape.n_v, np.uint8)
+        isc[list(shape.const)] = 1
+        return float(_L().rdfgen_tree_bound(self._h, shape.n_v, _ptr(se), _ptr(isc),
+                                            _ptr(q.embedding), _ptr(q.patterns),
+                                            _ptr(q.u_subject)))
 
     def sample(self, shape: Shape, seed: int, qid: int, cap: float, tries: int = 3,
                escalate: bool = True, work_cap: int = 0):
@@ -348,6 +378,72 @@ def batched_queries(w: Workload, sampler: Sampler, n: int | None = None,
 
     with cf.ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
         return list(ex.map(one, range(len(pairs))))
+
+
+def bandwidth_root(shape: Shape) -> int:
+    """The vertex the degree-driven traversal (Sec. 6.1.2) starts from in a
+    constant-free query: the most incident edges, ties to the lowest index
+    (shape vertex k is variable k here)."""
+    deg = [0] * shape.n_v
+    for u, v in shape.edges:
+        deg[u] += 1
+        deg[v] += 1
+    return max(range(shape.n_v), key=lambda v: (deg[v], -v))
+
+
+def _shapes_bandwidth(w: Workload, n: int):
+    """Constant-free cycles whose first evaluated group (the root's incident
+    edges) takes predicates among the 8 most frequent, so the root's
+    candidate set is large and its expansion reads many edges, while every
+    edge off the root and the pendant edge take predicates from the rarer
+    half (ids above P/2), which keeps the answer small. In turn: 4-cycle,
+    4-cycle with a pendant vertex on the root, 3-cycle, 5-cycle."""
+    top = (1, 8)
+    tail = (w.n_preds // 2 + 1, w.n_preds)
+    out = []
+    for q in range(n):
+        kind = q % 4
+        sh = cycle(4) if kind == 0 else cycle_leaf(4) if kind == 1 else cycle(3) if kind == 2 \
+            else cycle(5)
+        root = bandwidth_root(sh)
+        ring = sh.n_v - (1 if kind == 1 else 0)          # vertices on the cycle
+        for e, (u, v) in enumerate(sh.edges):
+            on_ring = u < ring and v < ring
+            sh.pred_range[e] = top if on_ring and root in (u, v) else tail
+        out.append(sh)
+    return out
+
+
+def bandwidth_queries(w: Workload, sampler: Sampler, n: int | None = None,
+                      cap: float | None = None, attempts: int = 4000):
+    """The bandwidth-bound workload: constant-free cycles (see
+    _shapes_bandwidth), each the first seeded embedding whose spanning-tree
+    bound (the path through the root's first edge, the rare edges and the
+    pendant edge) is at most cap, so its exact answer count is at most cap.
+    Every query has at least its embedding as an answer. Bounds depend only
+    on the predicates and directions and are cached on them."""
+    cap = w.cap if cap is None else cap
+    shapes = _shapes_bandwidth(w, w.n_queries if n is None else n)
+    cache = {}
+    out = []
+    for qi, sh in enumerate(shapes):
+        got = None
+        for a in range(attempts):
+            q = sampler.embed(sh, w.query_seed, qi * 100003 + a, with_bound=False)
+            if q is None:
+                continue
+            key = (tuple(q.patterns[:, 1].tolist()), tuple(q.u_subject.tolist()))
+            if key not in cache:
+                cache[key] = sampler.tree_bound(sh, q)
+            q.bound = cache[key]
+            if q.bound <= cap:
+                got = q
+                break
+        if got is None:
+            raise RuntimeError("no embedding of %s within bound %g in %d attempts"
+                               % (sh.name, cap, attempts))
+        out.append(got)
+    return out
 
 
 def queries(w: Workload, sampler: Sampler, n: int | None = None):

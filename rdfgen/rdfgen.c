@@ -209,13 +209,21 @@ rdf_adj* rdfgen_adj_build(const uint32_t* s, const uint32_t* p, const uint32_t* 
  *   is_const      per shape vertex: 1 = constant
  *   dir_req       per shape edge: 0 = any direction, 1 = u must be the subject,
  *                 2 = u must be the object (tree edges only)
+ *   plo, phi      per shape edge: its predicate must lie in plo[e]..phi[e]
+ *                 (both NULL: any predicate)
  *   patterns      out: n_se x 3 int64 (s, p, o); variables are -(k+1) with k
  *                 the rank of the shape vertex among non-constant ones
  *   mapped        out: the graph vertex of each shape vertex
  *   u_subject     out: per shape edge, 1 when its u end is the triple's subject
  * Returns 0 on success, 1 when this attempt found no embedding. */
+static inline int pred_ok(const rdf_adj* g, uint64_t t, const uint32_t* plo, const uint32_t* phi,
+                          uint32_t e) {
+    return !plo || (g->p[t] >= plo[e] && g->p[t] <= phi[e]);
+}
+
 int rdfgen_embed(const rdf_adj* g, uint32_t n_sv, uint32_t n_se, const uint32_t* se,
-                 const uint8_t* is_const, const uint8_t* dir_req, uint64_t seed, uint64_t attempt,
+                 const uint8_t* is_const, const uint8_t* dir_req, const uint32_t* plo,
+                 const uint32_t* phi, uint64_t seed, uint64_t attempt,
                  int64_t* patterns, uint32_t* mapped, uint8_t* u_subject) {
     if (g->n == 0 || n_sv == 0 || n_se + 1 < n_sv) return 1;
     const uint64_t kq = stream_key(seed, ST_QUERY);
@@ -236,11 +244,31 @@ int rdfgen_embed(const rdf_adj* g, uint32_t n_sv, uint32_t n_se, const uint32_t*
             if (dir_req[e] == 1) din = 0;
             if (dir_req[e] == 2) { dout = 0; }
             if (dout + din == 0) { ok = 0; break; }
-            uint64_t r = draw(kq, ctr++) % (dout + din);
-            if (dir_req[e] == 2) r += g->out_off[gu + 1] - g->out_off[gu];
             uint64_t dout_full = g->out_off[gu + 1] - g->out_off[gu];
-            if (r < dout_full) { ti = g->out_idx[g->out_off[gu] + r]; u_is_subject = 1; mv[w] = g->o[ti]; }
-            else { ti = g->in_idx[g->in_off[gu] + (r - dout_full)]; u_is_subject = 0; mv[w] = g->s[ti]; }
+            if (plo) {
+                /* uniform among the incident triples whose predicate is in range */
+                uint64_t cnt = 0;
+                for (uint64_t k = 0; k < dout; ++k) cnt += pred_ok(g, g->out_idx[g->out_off[gu] + k], plo, phi, e);
+                for (uint64_t k = 0; k < din; ++k) cnt += pred_ok(g, g->in_idx[g->in_off[gu] + k], plo, phi, e);
+                if (cnt == 0) { ok = 0; break; }
+                uint64_t pick = draw(kq, ctr++) % cnt;
+                ti = 0; u_is_subject = 1;
+                for (uint64_t k = 0; k < dout; ++k) {
+                    uint64_t t = g->out_idx[g->out_off[gu] + k];
+                    if (pred_ok(g, t, plo, phi, e)) { if (pick == 0) { ti = t; u_is_subject = 1; goto picked; } --pick; }
+                }
+                for (uint64_t k = 0; k < din; ++k) {
+                    uint64_t t = g->in_idx[g->in_off[gu] + k];
+                    if (pred_ok(g, t, plo, phi, e)) { if (pick == 0) { ti = t; u_is_subject = 0; goto picked; } --pick; }
+                }
+            picked:
+                mv[w] = u_is_subject ? g->o[ti] : g->s[ti];
+            } else {
+                uint64_t r = draw(kq, ctr++) % (dout + din);
+                if (dir_req[e] == 2) r += dout_full;
+                if (r < dout_full) { ti = g->out_idx[g->out_off[gu] + r]; u_is_subject = 1; mv[w] = g->o[ti]; }
+                else { ti = g->in_idx[g->in_off[gu] + (r - dout_full)]; u_is_subject = 0; mv[w] = g->s[ti]; }
+            }
         } else {                                   /* non-tree edge: both ends mapped */
             if (mv[u] < 0 || mv[w] < 0) { ok = 0; break; }
             gu = (uint64_t)mv[u];
@@ -248,18 +276,24 @@ int rdfgen_embed(const rdf_adj* g, uint32_t n_sv, uint32_t n_se, const uint32_t*
             uint64_t dout = g->out_off[gu + 1] - g->out_off[gu];
             uint64_t din = g->in_off[gu + 1] - g->in_off[gu];
             uint64_t cnt = 0;
-            for (uint64_t k = 0; k < dout; ++k) cnt += g->o[g->out_idx[g->out_off[gu] + k]] == gw;
-            for (uint64_t k = 0; k < din; ++k) cnt += g->s[g->in_idx[g->in_off[gu] + k]] == gw;
+            for (uint64_t k = 0; k < dout; ++k) {
+                uint64_t t = g->out_idx[g->out_off[gu] + k];
+                cnt += g->o[t] == gw && pred_ok(g, t, plo, phi, e);
+            }
+            for (uint64_t k = 0; k < din; ++k) {
+                uint64_t t = g->in_idx[g->in_off[gu] + k];
+                cnt += g->s[t] == gw && pred_ok(g, t, plo, phi, e);
+            }
             if (cnt == 0) { ok = 0; break; }
             uint64_t pick = draw(kq, ctr++) % cnt;
             ti = 0; u_is_subject = 1;
             for (uint64_t k = 0; k < dout; ++k) {
                 uint64_t t = g->out_idx[g->out_off[gu] + k];
-                if (g->o[t] == gw) { if (pick == 0) { ti = t; u_is_subject = 1; goto found; } --pick; }
+                if (g->o[t] == gw && pred_ok(g, t, plo, phi, e)) { if (pick == 0) { ti = t; u_is_subject = 1; goto found; } --pick; }
             }
             for (uint64_t k = 0; k < din; ++k) {
                 uint64_t t = g->in_idx[g->in_off[gu] + k];
-                if (g->s[t] == gw) { if (pick == 0) { ti = t; u_is_subject = 0; goto found; } --pick; }
+                if (g->s[t] == gw && pred_ok(g, t, plo, phi, e)) { if (pick == 0) { ti = t; u_is_subject = 0; goto found; } --pick; }
             }
         found:;
         }
