@@ -154,6 +154,20 @@ gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint
  * device memory until gs_free_result. */
 gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out);
 
+/* Estimated device memory of evaluating the plan alone on g (*bytes: the
+ * binding-tree levels of Sec. 7.1 with their scratch, the answer rows, and
+ * for a plan with a triple scan its candidate vectors and masks) and its
+ * estimated answer rows (*rows). Made on the host from per-predicate counts
+ * taken when the graph was loaded (entries per label, rows and columns
+ * holding each label), taking labels as independent of the structure: a
+ * level's nodes are the previous level's times the mean range length of
+ * the edge it expands, times the share of candidates that hold the
+ * predicates of the variable's other edges. It is an estimate, not a
+ * bound. The server admits queries by it, and gs_eval_query sizes its first
+ * workspace by it when it exceeds the default. Either out pointer may be
+ * NULL. */
+gs_status gs_plan_estimate(const gs_graph* g, const gs_plan* plan, uint64_t* bytes, double* rows);
+
 /* Number of answer rows and variables. Waits for the result's own work on
  * its stream (work enqueued on the stream after it is not waited for).
  * When the evaluation ran out of its device workspace it is re-run with a
@@ -274,15 +288,22 @@ void gs_free_batch(gs_batch* b);
 /* Serving loop (continuous batching). The server keeps the graph resident
  * and owns a worker thread and a pool of CUDA streams. Submitted plans wait
  * in arrival order; when the device is idle, when max_batch / 8 plans
- * wait, or when the oldest has waited max_wait_us, the worker admits the
- * waiting plans into a batch (as in gs_eval_batch) while the batch's
- * device-memory estimate (per-CTA
- * workspaces plus pool_bytes_per_query per query) fits the memory budget
- * together with the batches in flight, and a stream is free. Batches
- * admitted while others run overlap on the device; queries a batch hands
- * to the grid path run on the graph's side streams without holding up the
- * worker. Answers are identical to gs_eval_query's; they stay on the
- * device until the ticket is released.
+ * wait, or when the oldest has waited max_wait_us, the worker admits
+ * waiting plans into a batch (as in gs_eval_batch) while a stream is free
+ * and the batch's estimated device bytes fit the memory budget together
+ * with the batches in flight. A plan's bytes are its estimated
+ * intermediate results (gs_plan_estimate's model): for a plan the batch
+ * kernel evaluates, its estimated answer bytes (at most
+ * pool_bytes_per_query) as its share of the answer pool; for a grid-path
+ * plan, its candidate vectors and the first workspace it will take. A
+ * batch adds its CTA workspaces and, with plans that need a triple scan,
+ * the scan's masks. A plan that does not fit waits and later plans that do
+ * fit pass it, until it has waited 50 x max_wait_us (then nothing passes
+ * it); a plan too large for the budget on its own runs alone once nothing
+ * else is in flight. Batches admitted while others run overlap on the
+ * device; queries a batch hands to the grid path run on the graph's side
+ * streams without holding up the worker. Answers are identical to
+ * gs_eval_query's; they stay on the device until the ticket is released.
  * Submit / poll / fetch / release may be called from any host thread. */
 typedef struct gs_server gs_server;
 typedef struct {
@@ -292,7 +313,8 @@ typedef struct {
     uint32_t max_wait_us;            /* while batches run, the longest a
                                         queued query waits for more arrivals
                                         before it starts a batch (0: 200) */
-    uint64_t pool_bytes_per_query;   /* answer pool share (0: 16 MiB) */
+    uint64_t pool_bytes_per_query;   /* largest answer-pool share of one
+                                        query (0: 16 MiB) */
     gs_batch_config batch;           /* tunables of every batch (zero fields:
                                         defaults; pool_bytes is ignored) */
 } gs_server_config;
@@ -300,6 +322,10 @@ typedef struct {
 gs_status gs_server_start(gs_graph* g, const gs_server_config* cfg, gs_server** out);
 /* Queue one plan (the plan must outlive its ticket). */
 gs_status gs_server_submit(gs_server* s, const gs_plan* plan, uint64_t* ticket);
+/* Queue n plans at once, in array order (the worker sees all or none of
+ * them); tickets[i] receives plan i's ticket. */
+gs_status gs_server_submit_many(gs_server* s, const gs_plan* const* plans, uint32_t n,
+                                uint64_t* tickets);
 /* Non-blocking: *done = 1 when the answer is ready; then *rows and
  * *latency_us (submission to completion, host clock) are set (may be NULL). */
 gs_status gs_server_poll(gs_server* s, uint64_t ticket, int* done, uint64_t* rows,
@@ -309,6 +335,13 @@ gs_status gs_server_fetch(gs_server* s, uint64_t ticket, int32_t* dst, uint64_t 
                           int dst_on_device, int sort_rows);
 /* Drop a finished ticket and its device memory share. */
 gs_status gs_server_release(gs_server* s, uint64_t ticket);
+/* The batch that took a ticket (1-based sequence number, 0 while it waits)
+ * and the ticket's estimated device bytes. Either out pointer may be NULL. */
+gs_status gs_server_ticket(gs_server* s, uint64_t ticket, uint64_t* batch_seq,
+                           uint64_t* est_bytes);
+/* Admissions so far that took a plan ahead of an older waiting one, and the
+ * estimated bytes of the batches in flight now. Either may be NULL. */
+gs_status gs_server_admission(gs_server* s, uint64_t* passed, uint64_t* inflight_bytes);
 /* Queries completed, batches launched, peak admitted device bytes. */
 gs_status gs_server_stats(gs_server* s, uint64_t* completed, uint64_t* batches,
                           uint64_t* peak_bytes);
@@ -376,6 +409,47 @@ gs_status gs_scan_candidates_noalloc(gs_graph* g, const uint32_t* preds, const u
 /* Size in bytes of the static workspace of gs_scan_candidates_noalloc. */
 size_t gs_noalloc_scratch_bytes(void);
 
+/* ------------------------------------------------------------------ */
+/* Per-query light-weight sparse matrix (LSpM, Sec. 6.2): the RDF matrix
+ * reduced on the device, from the resident store, to the predicates a query
+ * uses. Row-wise it keeps the entries whose predicate is in row_preds and
+ * drops the rows left empty (Sec. 6.2.1 steps 1, 3, 4; Sec. 6.2.2's CSR
+ * part); column-wise it does the same with col_preds (Sec. 6.2.2's CSC
+ * part). Reduced rows keep the (label, other end) order.
+ *   row_preds, col_preds   host arrays of predicate ids in 1..P (repeats
+ *                          allowed; either may be empty)
+ * Synchronizes cuda_stream. The LSpM holds device memory until
+ * gs_free_lspm and must not outlive g. */
+typedef struct gs_lspm gs_lspm;
+gs_status gs_lspm_build(gs_graph* g, const uint32_t* row_preds, uint32_t n_row,
+                        const uint32_t* col_preds, uint32_t n_col, void* cuda_stream,
+                        gs_lspm** out);
+/* The LSpM of one plan (the degree-driven storage of Sec. 6.2.2): row-wise
+ * the predicates its evaluation reads from rows (edges expanded from or
+ * checked against a subject's row, pre-pruning of a variable's out-edges,
+ * the triple scan's row predicates), column-wise those it reads from
+ * columns. */
+gs_status gs_lspm_for_plan(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_lspm** out);
+/* Rows (by_column = 0) or columns (1) kept, and entries kept. Either out
+ * pointer may be NULL. */
+gs_status gs_lspm_info(const gs_lspm* l, int by_column, uint64_t* kept, uint64_t* nnz);
+/* The reduced orientation in the paper's arrays:
+ *   m[N+1]      Mr (Mc): m[i+1] - m[i] = 1 when row i is kept, and it is
+ *               then row m[i] of the reduced matrix
+ *   ptr[kept+1] Pr (Pc): the kept rows' entry ranges
+ *   val[nnz]    predicate of each entry; idx[nnz] its column (row) id
+ * Buffers are host memory unless dst_on_device. Synchronizes cuda_stream. */
+gs_status gs_lspm_export(const gs_lspm* l, int by_column, uint32_t* m, uint32_t* ptr,
+                         uint32_t* val, uint32_t* idx, int dst_on_device, void* cuda_stream);
+/* gs_eval_query on the LSpM instead of the full store (same answers).
+ * GS_EINVAL when l was built for another graph or lacks a (predicate,
+ * orientation) pair the plan reads. */
+gs_status gs_eval_query_lspm(gs_graph* g, const gs_lspm* l, const gs_plan* plan, void* cuda_stream,
+                             gs_result** out);
+void gs_free_lspm(gs_lspm* l);
+
+/* Frees the graph. Stop every server started on it (gs_server_stop) and
+ * free its results, batches and LSpMs first: they use its store. */
 void gs_free_graph(gs_graph* g);
 void gs_free_plan(gs_plan* plan);
 void gs_free_result(gs_result* r);

@@ -53,6 +53,8 @@ def _L():
                                  ctypes.POINTER(u64), ctypes.POINTER(u32)]
         lib.orc_free.restype = None
         lib.orc_free.argtypes = [vp]
+        lib.orc_count.restype = i32
+        lib.orc_count.argtypes = [vp, vp, u32, i32, u64, ctypes.POINTER(u64), ctypes.POINTER(u64)]
         _lib = lib
     return _lib
 
@@ -123,6 +125,23 @@ class Index:
             return buf.copy().reshape(nr, nk)
         finally:
             _L().orc_free(ctypes.cast(rows, ctypes.c_void_p))
+
+    def count(self, patterns, threads: int = 1, max_steps: int = 0):
+        """(answer rows, join steps, complete) of a BGP without storing the
+        rows; with max_steps > 0 the join gives up after about that many
+        steps (complete is then False and rows a lower bound)."""
+        pat = np.ascontiguousarray(np.asarray(patterns, np.int64).reshape(-1, 3))
+        n = ctypes.c_uint64()
+        st = ctypes.c_uint64()
+        rc = _L().orc_count(self._h, _ptr(pat), len(pat), int(threads), int(max_steps),
+                            ctypes.byref(n), ctypes.byref(st))
+        if rc == -1:
+            raise ValueError("invalid query")
+        if rc == -2:
+            raise MemoryError("oracle out of memory")
+        if rc not in (0, -4):
+            raise RuntimeError("oracle internal error %d" % rc)
+        return int(n.value), int(st.value), rc == 0
 
 
 def csr_arrays(s, p, o, n_rows: int):

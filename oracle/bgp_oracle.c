@@ -70,8 +70,34 @@ void orc_index_free(orc_index* ix) {
     free(ix->spo); free(ix->ops); free(ix->pso); free(ix->pcount); free(ix);
 }
 
+/* Sort t[0..n) by (a, b, c) when its entries are already grouped by a in
+ * the buckets off[0..n_keys]: each bucket is sorted on its own (in
+ * parallel; buckets are independent). */
+static void sort_buckets(tri* t, const uint64_t* off, uint64_t n_keys) {
+    #pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t k = 0; k < (int64_t)n_keys; ++k)
+        if (off[k + 1] - off[k] > 1) qsort(t + off[k], off[k + 1] - off[k], sizeof(tri), cmp_tri);
+}
+
+/* Bucket offsets of n entries by key key(i) < n_keys (a counting pass). */
+static uint64_t* bucket_offsets(uint64_t n_keys, uint64_t n, const uint32_t* key, uint64_t stride) {
+    uint64_t* off = (uint64_t*)calloc(n_keys + 1, sizeof(uint64_t));
+    if (!off) return NULL;
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)n; ++i) {
+        #pragma omp atomic
+        off[key[(uint64_t)i * stride] + 1]++;
+    }
+    for (uint64_t k = 0; k < n_keys; ++k) off[k + 1] += off[k];
+    return off;
+}
+
 /* Build the index. Returns NULL on a bad triple (vertex >= n_vertices or
- * predicate not in 1..n_preds) or when memory runs out. */
+ * predicate not in 1..n_preds) or when memory runs out. Each sorted copy is
+ * made by grouping the triples by their first field (a counting sort) and
+ * sorting every group by the other two; the (p, s, o) copy is a stable
+ * grouping of the (s, p, o) one by p, which keeps (s, o) order inside each
+ * group. */
 orc_index* orc_index_build(const uint32_t* s, const uint32_t* p, const uint32_t* o, uint64_t n,
                            uint32_t n_vertices, uint32_t n_preds) {
     for (uint64_t i = 0; i < n; ++i)
@@ -82,25 +108,49 @@ orc_index* orc_index_build(const uint32_t* s, const uint32_t* p, const uint32_t*
     uint64_t cap = n ? n : 1;
     ix->spo = (tri*)malloc(sizeof(tri) * cap);
     ix->pcount = (uint64_t*)calloc((size_t)n_preds + 1, sizeof(uint64_t));
-    if (!ix->spo || !ix->pcount) { orc_index_free(ix); return NULL; }
-    for (uint64_t i = 0; i < n; ++i) { ix->spo[i].a = s[i]; ix->spo[i].b = p[i]; ix->spo[i].c = o[i]; }
-    qsort(ix->spo, n, sizeof(tri), cmp_tri);
+    uint64_t* off = bucket_offsets(n_vertices, n, s, 1);
+    const uint64_t n_cur = (n_vertices > n_preds ? n_vertices : n_preds) + 1ull;
+    uint64_t* cur = (uint64_t*)malloc(sizeof(uint64_t) * n_cur);
+    if (!ix->spo || !ix->pcount || !off || !cur) { free(off); free(cur); orc_index_free(ix); return NULL; }
+    memcpy(cur, off, sizeof(uint64_t) * n_vertices);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)n; ++i) {
+        uint64_t at;
+        #pragma omp atomic capture
+        at = cur[s[i]]++;
+        ix->spo[at].a = s[i]; ix->spo[at].b = p[i]; ix->spo[at].c = o[i];
+    }
+    sort_buckets(ix->spo, off, n_vertices);
     uint64_t m = 0;
     for (uint64_t i = 0; i < n; ++i)
         if (m == 0 || cmp_tri(&ix->spo[m - 1], &ix->spo[i]) != 0) ix->spo[m++] = ix->spo[i];
     ix->n = m;
+    free(off);
     cap = m ? m : 1;
     ix->ops = (tri*)malloc(sizeof(tri) * cap);
     ix->pso = (tri*)malloc(sizeof(tri) * cap);
-    if (!ix->ops || !ix->pso) { orc_index_free(ix); return NULL; }
-    for (uint64_t i = 0; i < m; ++i) {
+    off = bucket_offsets(n_vertices, m, &ix->spo[0].c, 3);
+    if (!ix->ops || !ix->pso || !off) { free(off); free(cur); orc_index_free(ix); return NULL; }
+    memcpy(cur, off, sizeof(uint64_t) * n_vertices);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)m; ++i) {
         tri t = ix->spo[i];
-        ix->ops[i].a = t.c; ix->ops[i].b = t.b; ix->ops[i].c = t.a;
-        ix->pso[i].a = t.b; ix->pso[i].b = t.a; ix->pso[i].c = t.c;
-        ix->pcount[t.b]++;
+        uint64_t at;
+        #pragma omp atomic capture
+        at = cur[t.c]++;
+        ix->ops[at].a = t.c; ix->ops[at].b = t.b; ix->ops[at].c = t.a;
     }
-    qsort(ix->ops, m, sizeof(tri), cmp_tri);
-    qsort(ix->pso, m, sizeof(tri), cmp_tri);
+    sort_buckets(ix->ops, off, n_vertices);
+    free(off);
+    for (uint64_t i = 0; i < m; ++i) ix->pcount[ix->spo[i].b]++;
+    uint64_t acc = 0;
+    for (uint32_t q = 0; q <= n_preds; ++q) { cur[q] = acc; acc += ix->pcount[q]; }
+    for (uint64_t i = 0; i < m; ++i) {   /* stable: (s, o) order stays inside each p */
+        tri t = ix->spo[i];
+        uint64_t at = cur[t.b]++;
+        ix->pso[at].a = t.b; ix->pso[at].b = t.a; ix->pso[at].c = t.c;
+    }
+    free(cur);
     return ix;
 }
 
@@ -167,9 +217,13 @@ typedef struct {
     uint64_t n, cap;
     uint32_t k;
     int oom;
+    int count_only;          /* count the rows, store none */
+    uint64_t steps, max_steps;   /* join calls made; give up past max_steps (0: no limit) */
+    int stop;
 } rowbuf;
 
 static void emit(rowbuf* rb, const int64_t* mu) {
+    if (rb->count_only) { rb->n++; return; }
     if (rb->oom) return;
     if (rb->n == rb->cap) {
         uint64_t nc = rb->cap ? rb->cap * 2 : 1024;
@@ -190,6 +244,8 @@ typedef struct {
 static int var_of(int64_t x) { return x < 0 ? (int)(-x - 1) : -1; }
 
 static void join(const join_t* J, uint32_t d, int64_t* mu, rowbuf* rb) {
+    if (rb->stop) return;
+    if (rb->max_steps && ++rb->steps > rb->max_steps) { rb->stop = 1; return; }
     if (d == J->n_pat) { emit(rb, mu); return; }
     const pat_t* q = &J->order[d];
     const orc_index* ix = J->ix;
@@ -230,16 +286,9 @@ static int cmp_row(const void* x, const void* y) {
     return 0;
 }
 
-/* Evaluate a BGP.
- *   patterns   n_pat x 3 int64 (s, p, o): s, o >= 0 constant vertex id,
- *              < 0 variable -(k+1); p a predicate id in 1..n_preds.
- *   threads    OpenMP threads for the first pattern's candidates (>= 1).
- *   rows_out   malloc'd int32 rows (n_rows x n_vars), caller frees with orc_free.
- * Returns 0; -1 bad query (no variables, variable ids not dense, bad
- * predicate or vertex); -2 out of memory; -3 a duplicate row (a bug). */
-int orc_eval(const orc_index* ix, const int64_t* patterns, uint32_t n_pat, int threads,
-             int32_t** rows_out, uint64_t* n_rows, uint32_t* n_vars) {
-    *rows_out = NULL; *n_rows = 0; *n_vars = 0;
+/* Checks the query and orders its patterns (step 2). Returns the number of
+ * variables, or -1 for a bad query. */
+static int prepare(const orc_index* ix, const int64_t* patterns, uint32_t n_pat, pat_t* order) {
     if (n_pat == 0 || n_pat > MAXPAT) return -1;
     int used[MAXVAR] = {0};
     int k = 0;
@@ -262,7 +311,6 @@ int orc_eval(const orc_index* ix, const int64_t* patterns, uint32_t n_pat, int t
     for (int v = 0; v < k; ++v) if (!used[v]) return -1;
 
     /* join order (step 2) */
-    pat_t order[MAXPAT];
     int taken[MAXPAT] = {0}, bound[MAXVAR] = {0};
     for (uint32_t d = 0; d < n_pat; ++d) {
         int best = -1, best_b = -1; uint64_t best_c = 0;
@@ -278,11 +326,14 @@ int orc_eval(const orc_index* ix, const int64_t* patterns, uint32_t n_pat, int t
         if (vs >= 0) bound[vs] = 1;
         if (vo >= 0) bound[vo] = 1;
     }
+    return k;
+}
 
+/* Step 3 over the ordered patterns into one buffer per thread (the first
+ * pattern's candidates split among the threads). */
+static void run_join(const orc_index* ix, const pat_t* order, uint32_t n_pat, int k, int threads,
+                     rowbuf* bufs) {
     join_t J = {ix, order, n_pat};
-    if (threads < 1) threads = 1;
-    rowbuf* bufs = (rowbuf*)calloc((size_t)threads, sizeof(rowbuf));
-    for (int t = 0; t < threads; ++t) bufs[t].k = (uint32_t)k;
 
     /* split the first pattern's candidates among threads */
     const pat_t* q0 = &order[0];
@@ -318,6 +369,26 @@ int orc_eval(const orc_index* ix, const int64_t* patterns, uint32_t n_pat, int t
             join(&J, 1, mu, &bufs[t]);
         }
     }
+}
+
+/* Evaluate a BGP.
+ *   patterns   n_pat x 3 int64 (s, p, o): s, o >= 0 constant vertex id,
+ *              < 0 variable -(k+1); p a predicate id in 1..n_preds.
+ *   threads    OpenMP threads for the first pattern's candidates (>= 1).
+ *   rows_out   malloc'd int32 rows (n_rows x n_vars), caller frees with orc_free.
+ * Returns 0; -1 bad query (no variables, variable ids not dense, bad
+ * predicate or vertex); -2 out of memory; -3 a duplicate row (a bug). */
+int orc_eval(const orc_index* ix, const int64_t* patterns, uint32_t n_pat, int threads,
+             int32_t** rows_out, uint64_t* n_rows, uint32_t* n_vars) {
+    *rows_out = NULL; *n_rows = 0; *n_vars = 0;
+    pat_t order[MAXPAT];
+    const int k = prepare(ix, patterns, n_pat, order);
+    if (k < 0) return -1;
+    if (threads < 1) threads = 1;
+    rowbuf* bufs = (rowbuf*)calloc((size_t)threads, sizeof(rowbuf));
+    if (!bufs) return -2;
+    for (int t = 0; t < threads; ++t) bufs[t].k = (uint32_t)k;
+    run_join(ix, order, n_pat, k, threads, bufs);
 
     uint64_t total = 0; int oom = 0;
     for (int t = 0; t < threads; ++t) { total += bufs[t].n; oom |= bufs[t].oom; }
@@ -340,3 +411,34 @@ int orc_eval(const orc_index* ix, const int64_t* patterns, uint32_t n_pat, int t
 }
 
 void orc_free(void* p) { free(p); }
+
+/* The number of answer rows of a BGP (as orc_eval, without storing them),
+ * giving up when the join makes more than max_steps calls (0: no limit) over
+ * all threads: a measure of the work the query takes here.
+ * Returns 0; -1 bad query; -2 out of memory; -4 the step limit was reached
+ * (*n_rows is then a lower bound). *steps gets the calls made (may be NULL). */
+int orc_count(const orc_index* ix, const int64_t* patterns, uint32_t n_pat, int threads,
+              uint64_t max_steps, uint64_t* n_rows, uint64_t* steps) {
+    *n_rows = 0;
+    if (steps) *steps = 0;
+    pat_t order[MAXPAT];
+    const int k = prepare(ix, patterns, n_pat, order);
+    if (k < 0) return -1;
+    if (threads < 1) threads = 1;
+    rowbuf* bufs = (rowbuf*)calloc((size_t)threads, sizeof(rowbuf));
+    if (!bufs) return -2;
+    for (int t = 0; t < threads; ++t) {
+        bufs[t].k = (uint32_t)k;
+        bufs[t].count_only = 1;
+        bufs[t].max_steps = max_steps ? (max_steps + threads - 1) / threads : 0;
+    }
+    run_join(ix, order, n_pat, k, threads, bufs);
+    int stopped = 0;
+    for (int t = 0; t < threads; ++t) {
+        *n_rows += bufs[t].n;
+        if (steps) *steps += bufs[t].steps;
+        stopped |= bufs[t].stop;
+    }
+    free(bufs);
+    return stopped ? -4 : 0;
+}

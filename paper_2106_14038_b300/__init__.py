@@ -8,15 +8,17 @@ fallback: without the built library, or without a GPU, calls raise.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
 from ._build import LIB, build
 
 __all__ = ["Graph", "Plan", "Result", "Batch", "Server", "GsError", "TorchAllocator", "load_library", "PLAN_DEGREE",
-           "PLAN_DIRECTION", "PLAN_LISTS", "BatchConfig", "build"]
+           "PLAN_DIRECTION", "PLAN_LISTS", "BatchConfig", "Lspm", "build"]
 
 PLAN_DEGREE = 0
 PLAN_DIRECTION = 1
@@ -32,7 +34,10 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_server_start", "gs_server_submit", "gs_server_poll", "gs_server_fetch",
             "gs_server_release", "gs_server_stats", "gs_server_stop",
             "gs_scan_candidates_noalloc", "gs_noalloc_scratch_bytes", "gs_eval_batch_cfg",
-            "gs_batch_autotune", "gs_server_replay", "gs_scan_status", "gs_batch_scans"]
+            "gs_batch_autotune", "gs_server_replay", "gs_scan_status", "gs_batch_scans",
+            "gs_plan_estimate", "gs_server_ticket", "gs_server_admission",
+            "gs_server_submit_many", "gs_lspm_build", "gs_lspm_for_plan", "gs_lspm_info",
+            "gs_lspm_export", "gs_eval_query_lspm", "gs_free_lspm"]
 
 
 class GsError(RuntimeError):
@@ -95,6 +100,17 @@ class TorchAllocator:
 
 
 _lib = None
+_live_servers = weakref.WeakSet()   # stopped before their graph is freed, and at exit
+_live_lspm = weakref.WeakSet()      # freed before their graph
+
+
+def _stop_servers(graph=None):
+    for srv in list(_live_servers):
+        if graph is None or srv._graph is graph:
+            srv.stop()
+
+
+atexit.register(_stop_servers)
 
 
 def load_library(path: str | None = None):
@@ -131,19 +147,28 @@ def load_library(path: str | None = None):
         "gs_batch_stats": [vp, P(ctypes.c_float), P(u32), P(u32)],
         "gs_batch_poll": [vp, P(i32)],
         "gs_batch_scans": [vp, P(u32), P(u32)],
+        "gs_plan_estimate": [vp, vp, P(u64), P(ctypes.c_double)],
         "gs_server_start": [vp, vp, P(vp)],
         "gs_server_submit": [vp, vp, P(u64)],
         "gs_server_poll": [vp, u64, P(i32), P(u64), P(ctypes.c_double)],
         "gs_server_fetch": [vp, u64, vp, u64, i32, i32],
         "gs_server_release": [vp, u64],
         "gs_server_stats": [vp, P(u64), P(u64), P(u64)],
+        "gs_server_ticket": [vp, u64, P(u64), P(u64)],
+        "gs_server_submit_many": [vp, vp, u32, vp],
+        "gs_lspm_build": [vp, vp, u32, vp, u32, vp, P(vp)],
+        "gs_lspm_for_plan": [vp, vp, vp, P(vp)],
+        "gs_lspm_info": [vp, i32, P(u64), P(u64)],
+        "gs_lspm_export": [vp, i32, vp, vp, vp, vp, i32, vp],
+        "gs_eval_query_lspm": [vp, vp, vp, vp, P(vp)],
+        "gs_server_admission": [vp, P(u64), P(u64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = i32
     for name in ("gs_free_graph", "gs_free_plan", "gs_free_result", "gs_free_batch",
-                 "gs_server_stop"):
+                 "gs_server_stop", "gs_free_lspm"):
         f = getattr(lib, name)
         f.argtypes = [vp]
         f.restype = None
@@ -208,6 +233,10 @@ class Graph:
 
     def close(self):
         if getattr(self, "_h", None):
+            _stop_servers(self)          # a running server uses the graph
+            for l in list(_live_lspm):   # so does a reduced matrix
+                if l._graph is self:
+                    l.close()
             _lib.gs_free_graph(self._h)
             self._h = None
 
@@ -318,11 +347,75 @@ class Graph:
         return out
 
 
+    def estimate(self, plan):
+        """(estimated device bytes, estimated answer rows) of evaluating plan."""
+        b, r = ctypes.c_uint64(), ctypes.c_double()
+        _check(_lib.gs_plan_estimate(self._h, plan._h, ctypes.byref(b), ctypes.byref(r)))
+        return int(b.value), float(r.value)
+
     def scan_status(self, stream=None):
         """Synchronize the stream; raise GsError (GS_ETIMEOUT) when a bounded
         wait of a scan()/scan_noalloc() call on this graph ran out since the
         last check (that scan's bits are incomplete)."""
         _check(_lib.gs_scan_status(self._h, _stream_handle(stream)))
+
+
+class Lspm:
+    """Per-query light-weight sparse matrix (Sec. 6.2) reduced on the device
+    from a graph: Lspm(graph, row_preds, col_preds) or Lspm.for_plan(plan)."""
+
+    def __init__(self, graph: Graph, row_preds=(), col_preds=(), stream=None, _plan=None):
+        h = ctypes.c_void_p()
+        if _plan is not None:
+            _check(_lib.gs_lspm_for_plan(graph._h, _plan._h, _stream_handle(stream), ctypes.byref(h)))
+        else:
+            r, c = _host_u32(list(row_preds)), _host_u32(list(col_preds))
+            _check(_lib.gs_lspm_build(graph._h, r.ctypes.data_as(ctypes.c_void_p), len(r),
+                                      c.ctypes.data_as(ctypes.c_void_p), len(c),
+                                      _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self._graph = graph
+        _live_lspm.add(self)
+
+    @classmethod
+    def for_plan(cls, graph: Graph, plan: "Plan", stream=None) -> "Lspm":
+        return cls(graph, stream=stream, _plan=plan)
+
+    def info(self, by_column: bool = False):
+        """(rows or columns kept, entries kept)."""
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib.gs_lspm_info(self._h, int(by_column), ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
+
+    def export(self, by_column: bool = False, stream=None):
+        """(M, P, Val, Idx) numpy arrays: Mr/Pr/Val/Col (or Mc/Pc/Val/Row)."""
+        kept, nnz = self.info(by_column)
+        m = np.empty(self._graph.n_vertices + 1, np.uint32)
+        ptr = np.empty(kept + 1, np.uint32)
+        val = np.empty(max(nnz, 1), np.uint32)
+        idx = np.empty(max(nnz, 1), np.uint32)
+        _check(_lib.gs_lspm_export(self._h, int(by_column), m.ctypes.data_as(ctypes.c_void_p),
+                                   ptr.ctypes.data_as(ctypes.c_void_p),
+                                   val.ctypes.data_as(ctypes.c_void_p),
+                                   idx.ctypes.data_as(ctypes.c_void_p), 0, _stream_handle(stream)))
+        return m, ptr, val[:nnz], idx[:nnz]
+
+    def eval(self, plan: "Plan", stream=None) -> "Result":
+        h = ctypes.c_void_p()
+        _check(_lib.gs_eval_query_lspm(self._graph._h, self._h, plan._h, _stream_handle(stream),
+                                       ctypes.byref(h)))
+        return Result(h, plan)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.gs_free_lspm(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:
@@ -447,12 +540,22 @@ class Server:
         self._h = h
         self._graph = graph
         self._plans = {}
+        _live_servers.add(self)
 
     def submit(self, plan: "Plan") -> int:
         t = ctypes.c_uint64()
         _check(_lib.gs_server_submit(self._h, plan._h, ctypes.byref(t)))
         self._plans[t.value] = plan
         return int(t.value)
+
+    def submit_many(self, plans):
+        """Queue several plans at once (the worker sees all or none)."""
+        arr = (ctypes.c_void_p * max(1, len(plans)))(*[p._h.value for p in plans])
+        out = np.zeros(max(1, len(plans)), np.uint64)
+        _check(_lib.gs_server_submit_many(self._h, arr, len(plans), out.ctypes.data_as(ctypes.c_void_p)))
+        for t, p in zip(out[:len(plans)].tolist(), plans):
+            self._plans[int(t)] = p
+        return [int(t) for t in out[:len(plans)]]
 
     def poll(self, ticket: int):
         """(done, rows, latency_us)."""
@@ -476,6 +579,18 @@ class Server:
     def release(self, ticket: int):
         _check(_lib.gs_server_release(self._h, ticket))
         self._plans.pop(ticket, None)
+
+    def ticket(self, ticket: int):
+        """(sequence number of the batch that took it, estimated device bytes)."""
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib.gs_server_ticket(self._h, ticket, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
+
+    def admission(self):
+        """(admissions that passed an older waiting query, bytes in flight)."""
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib.gs_server_admission(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
     def stats(self):
         """(completed queries, batches launched, peak admitted device bytes)."""

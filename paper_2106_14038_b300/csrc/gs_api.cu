@@ -80,6 +80,9 @@ struct gs_result {
     // its completion event and status word (NULL: the query scans itself)
     cudaEvent_t scan_ready = nullptr;
     const uint32_t* scan_status = nullptr;
+    // the orientations evaluated against (a per-query LSpM; NULL: the graph's)
+    const Store* so = nullptr;
+    const Store* si = nullptr;
     uint32_t launches = 0;
     uint64_t rows = 0;
     uint64_t out_off = 0;
@@ -140,8 +143,8 @@ ExecDev exec_view(gs_result* r) {
     E.arena = r->arena;
     E.arena_bytes = r->arena_bytes;
     E.ctl = (Ctl*)r->arena;
-    E.out = dview(r->g->out);
-    E.in = dview(r->g->in);
+    E.out = dview(r->so ? *r->so : r->g->out);
+    E.in = dview(r->si ? *r->si : r->g->in);
     E.bits = r->bits;
     E.words = (r->g->N + 31) / 32;
     E.lists = r->lists;
@@ -155,7 +158,7 @@ gs_status enqueue(gs_result* r) {
     gs_status rc = r->mode == 1
         ? enqueue_small(&r->plan, exec_view(r), &r->launches, r->st)
         : enqueue_eval(r->g, &r->plan, exec_view(r), r->work, &r->launches, r->st, r->resume,
-                       r->scan_status);
+                       r->scan_status, r->so, r->si);
     if (rc != GS_OK) return rc;
     GS_CUDA(cudaEventRecord(r->ev1, r->st));
     // the head of the control block follows the kernels to pinned memory
@@ -385,6 +388,75 @@ gs_status gs::scan_spec_from(const gs_graph* g, const uint32_t* preds, const uin
     return GS_OK;
 }
 
+void gs::plan_estimate(const gs_graph* g, const gs_plan* P, Estimate* e) {
+    *e = Estimate{};
+    const double N = std::max(1.0, (double)g->N), M = std::max(1.0, (double)g->M);
+    auto stat = [&](const std::vector<uint64_t>& v, uint32_t p) -> double {
+        return p < v.size() ? (double)v[p] : 0.0;
+    };
+    // mean range length of label p in a row (dir 0) / column (dir 1) holding it
+    auto fanout = [&](uint32_t p, uint32_t dir) {
+        const double r = stat(g->lab_rows[dir], p);
+        return r > 0 ? stat(g->lab_cnt[dir], p) / r : 0.0;
+    };
+    // share of vertices whose row (dir 0) / column (dir 1) holds label p
+    auto holds = [&](uint32_t p, uint32_t dir) { return stat(g->lab_rows[dir], p) / N; };
+    const size_t np = P->patterns.size() / 3;
+    double prev = 1.0, worst_scratch = 0.0;
+    uint64_t levels = 0;
+    for (int l = 0; l < P->n_levels; ++l) {
+        const LevelSpec& L = P->levels[l];
+        const int w = L.var;
+        double cand, pass = 1.0;
+        int src = -1;
+        if (L.src == kSrcList) {
+            cand = N;
+        } else {
+            cand = 1e300;
+            for (int b = 0; b < L.n_binders; ++b) {
+                const Binder& B = L.b[b];
+                double f = fanout(B.label, B.dir);
+                if (B.from_const) {   // the constant's row length x the label's share
+                    const std::vector<uint32_t>& deg = B.dir == 0 ? g->deg_out : g->deg_in;
+                    f = B.c < deg.size() ? std::max(1.0, deg[B.c] * stat(g->lab_cnt[B.dir], B.label) / M) : 0.0;
+                }
+                if (f < cand) { cand = f; src = b; }
+            }
+            for (int b = 0; b < L.n_binders; ++b)
+                if (b != src) pass *= std::min(1.0, fanout(L.b[b].label, L.b[b].dir) / N);
+        }
+        // the variable's other patterns: its candidates must hold their predicates
+        for (size_t i = 0; i < np; ++i) {
+            const int64_t s = P->patterns[3 * i], o = P->patterns[3 * i + 2];
+            const uint32_t p = (uint32_t)P->patterns[3 * i + 1];
+            const bool subj = s == -(int64_t)w - 1, obj = o == -(int64_t)w - 1;
+            if (!subj && !obj) continue;
+            bool binder = false;   // edges to bound ends are the binders above
+            for (int b = 0; b < L.n_binders && !binder; ++b)
+                binder = L.b[b].label == p && ((L.b[b].dir == 0 && obj) || (L.b[b].dir == 1 && subj));
+            if (binder) continue;
+            if (subj) pass *= holds(p, 0);
+            if (obj && !subj) pass *= holds(p, 1);
+        }
+        const double nodes = std::min(1e15, prev * cand * pass);
+        e->nodes[l] = nodes;
+        const uint32_t nbm = std::max(1, L.n_binders);
+        worst_scratch = std::max(worst_scratch, prev * (16.0 + 8.0 * nbm));
+        levels += (((uint64_t)(8.0 * nodes) + 8 + 255) & ~255ull);
+        prev = nodes;
+    }
+    double rows = P->n_levels ? prev : 0.0;
+    for (int j = 0; j < P->n_leaves; ++j) rows *= fanout(P->leaves[j].label, P->leaves[j].dir);
+    rows = std::min(rows, 1e15);
+    e->rows = rows;
+    worst_scratch = std::max(worst_scratch, prev * (8.0 + 8.0 * std::max(1, P->n_leaves)));
+    e->answer = (uint64_t)(4.0 * P->n_vars * rows);
+    e->arena = kCtlBytes + levels + (uint64_t)worst_scratch + e->answer;
+    const uint64_t words = (g->N + 31) / 32;
+    e->vectors = P->needs_scan ? 4ull * words * (uint64_t)std::max(1, P->scan.n_bvars) : 0;
+    e->total = e->arena + e->vectors;
+}
+
 // An upper bound on the candidates of the plan's first level when it is
 // seeded from constants (their row or column lengths), else UINT64_MAX.
 uint64_t gs::first_level_bound(const gs_graph* g, const gs_plan* plan) {
@@ -436,7 +508,7 @@ namespace {
 
 gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
                           uint32_t* pre_bits, cudaEvent_t pre_ready, const uint32_t* pre_status,
-                          gs_result** out);
+                          gs_result** out, const Store* so = nullptr, const Store* si = nullptr);
 
 }  // namespace
 
@@ -459,7 +531,7 @@ namespace {
 
 gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
                           uint32_t* pre_bits, cudaEvent_t pre_ready, const uint32_t* pre_status,
-                          gs_result** out) {
+                          gs_result** out, const Store* so, const Store* si) {
     if (!g || !plan || !out) { set_error("gs_eval_query: NULL argument"); return GS_EINVAL; }
     *out = nullptr;
     if (plan->N == 0) {   // planned without a graph: check the ids now
@@ -483,6 +555,8 @@ gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, i
     r->g = g;
     r->plan = *plan;
     r->st = (cudaStream_t)cuda_stream;
+    r->so = so;
+    r->si = si;
     const uint64_t words = (g->N + 31) / 32;
     gs_status rc = GS_OK;
     cudaEvent_t* ev[3] = {&r->ev0, &r->ev1, &r->ev2};
@@ -511,11 +585,9 @@ gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, i
     if (rc == GS_OK) {
         // the grid path's size for both: a query the single-CTA kernel hands
         // back continues in this workspace
-        uint64_t want = std::max<uint64_t>(kArenaMin, std::min<uint64_t>(kArenaDefault, free_device_bytes(g) / 8));
-        if (const char* env = getenv("GS_ARENA_BYTES")) {   // initial workspace size
-            unsigned long long v = strtoull(env, nullptr, 10);
-            if (v >= 4096) want = v;
-        }
+        Estimate est;
+        plan_estimate(g, plan, &est);
+        const uint64_t want = first_arena_bytes(g, est);
         r->arena = (uint8_t*)g->alloc.get(want, r->st);
         r->arena_bytes = want;
         if (!r->arena) { set_error("gs_eval_query: cannot allocate the workspace"); rc = GS_ENOMEM; }
@@ -533,6 +605,49 @@ extern "C" {
 gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out) {
     const char* how = getenv("GS_EXEC");   // "grid" forces the grid path
     return eval_query_path(g, plan, cuda_stream, how && !strcmp(how, "grid"), out);
+}
+
+}  // extern "C"
+
+uint64_t gs::first_arena_bytes(gs_graph* g, const Estimate& est) {
+    if (const char* env = getenv("GS_ARENA_BYTES")) {   // initial workspace size
+        unsigned long long v = strtoull(env, nullptr, 10);
+        if (v >= 4096) return v;
+    }
+    const uint64_t free_b = free_device_bytes(g);
+    uint64_t want = std::max<uint64_t>(kArenaMin, std::min<uint64_t>(kArenaDefault, free_b / 8));
+    if (est.arena > want)   // a larger first workspace saves re-runs
+        want = std::max(want, std::min<uint64_t>(est.arena + est.arena / 4, free_b / 4));
+    return want;
+}
+
+extern "C" {
+
+gs_status gs_plan_estimate(const gs_graph* g, const gs_plan* plan, uint64_t* bytes, double* rows) {
+    if (!g || !plan) { set_error("gs_plan_estimate: NULL argument"); return GS_EINVAL; }
+    if (plan->N != 0 && (plan->N != g->N || plan->P != g->P)) {
+        set_error("gs_plan_estimate: the plan was made for another graph");
+        return GS_EINVAL;
+    }
+    Estimate e;
+    plan_estimate(g, plan, &e);
+    if (bytes) *bytes = e.total + (plan->needs_scan ? scan_work_bytes(g) : 0);
+    if (rows) *rows = e.rows;
+    return GS_OK;
+}
+
+gs_status gs_eval_query_lspm(gs_graph* g, const gs_lspm* l, const gs_plan* plan, void* cuda_stream,
+                             gs_result** out) {
+    if (!g || !l || !plan || !out) { set_error("gs_eval_query_lspm: NULL argument"); return GS_EINVAL; }
+    *out = nullptr;
+    if (lspm_graph(l) != g) { set_error("gs_eval_query_lspm: the LSpM was built for another graph"); return GS_EINVAL; }
+    if (!lspm_covers(l, plan)) {
+        set_error("gs_eval_query_lspm: the LSpM lacks a (predicate, orientation) the plan reads");
+        return GS_EINVAL;
+    }
+    const char* how = getenv("GS_EXEC");   // "grid" forces the grid path
+    return eval_query_impl(g, plan, cuda_stream, how && !strcmp(how, "grid"), nullptr, nullptr,
+                           nullptr, out, lspm_side(l, 0), lspm_side(l, 1));
 }
 
 gs_status gs_result_info(gs_result* r, uint64_t* n_rows, uint32_t* n_vars) {

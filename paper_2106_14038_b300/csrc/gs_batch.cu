@@ -321,7 +321,7 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
     for (uint32_t q = 0; q < n; ++q) {
         b->n_vars[q] = plans[q]->n_vars;
         // a first level certainly past the candidate budget goes to the grid path
-        if (rec_fits(plans[q]) && first_level_bound(g, plans[q]) <= 8 * b->cfg.cand_budget) {
+        if (batch_in_kernel(g, plans[q], &b->cfg)) {
             b->in_kernel[q] = 1;
             off[n_in] = total;
             b->kidx.push_back(q);
@@ -467,13 +467,19 @@ uint64_t gs::batch_device_bytes(const gs_batch* b) {
     return b->slot_bytes * (uint64_t)b->blocks + b->pool_bytes;
 }
 
-uint64_t gs::batch_estimate(const gs_graph* g, const gs_batch_config* cfg, uint32_t n,
-                            uint64_t pool_bytes) {
-    const gs_batch_config c = resolve(g, cfg);
-    const uint64_t blocks = std::min<uint64_t>(n, (uint64_t)g->sm_count * c.blocks_per_sm);
-    // plus the grid-path queries it may run at once (workspace and scan masks)
-    const uint64_t grid = (uint64_t)c.grid_streams * ((512ull << 20) + scan_work_bytes(g));
-    return blocks * slot_bytes_for(c.cand_budget) + pool_bytes + grid;
+bool gs::batch_in_kernel(const gs_graph* g, const gs_plan* P, const gs_batch_config* cfg) {
+    const uint64_t cand = cfg && cfg->cand_budget ? cfg->cand_budget : kBatchCand;
+    // a first level certainly past the candidate budget goes to the grid path
+    return rec_fits(P) && first_level_bound(g, P) <= 8 * cand;
+}
+
+uint64_t gs::batch_fixed_bytes(const gs_graph* g, const gs_batch_config* cfg, uint32_t n_kernel,
+                               bool has_scan) {
+    const uint32_t fit = (uint32_t)batch_blocks_per_sm();
+    const uint32_t bps = cfg && cfg->blocks_per_sm ? std::min(cfg->blocks_per_sm, fit) : fit;
+    const uint64_t cand = cfg && cfg->cand_budget ? cfg->cand_budget : kBatchCand;
+    const uint64_t blocks = std::min<uint64_t>(n_kernel, (uint64_t)g->sm_count * std::max(1u, bps));
+    return blocks * slot_bytes_for(cand) + (has_scan ? scan_work_bytes(g, true) : 0);
 }
 
 gs_status gs::batch_advance(gs_batch* b, int* done) {

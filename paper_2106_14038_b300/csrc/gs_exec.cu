@@ -390,7 +390,8 @@ uint64_t host_level_off(const uint64_t* n, int l) {
 }
 
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
-                       cudaStream_t st, int start_level, const uint32_t* scanned) {
+                       cudaStream_t st, int start_level, const uint32_t* scanned, const Store* so,
+                       const Store* si) {
     const dim3 nb(g->n_blocks), th(kThreads);
     Ctl* ctl = E.ctl;
     uint32_t nl_launch = 1;
@@ -407,7 +408,7 @@ gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, vo
         for (uint32_t i = 0; i < 3 * cc.n; ++i) cc.t[i] = P->const_triples[i];
         k_init<<<1, kThreads, 0, st>>>(E, cc, scanned);   // zeroes the control block's head
         if (P->needs_scan && !scanned) {
-            gs_status rc = run_scan(g, P->scan, E.bits, scan_work, st, &ctl->status);
+            gs_status rc = run_scan(g, P->scan, E.bits, scan_work, st, &ctl->status, so, si);
             if (rc != GS_OK) return rc;
             nl_launch += 3;
         }

@@ -108,9 +108,14 @@ gs_status eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_stream, i
 gs_status eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n, void* cuda_stream,
                         const gs_batch_config* cfg, int max_blocks, gs_batch** out);
 uint64_t batch_device_bytes(const gs_batch* b);
-// Device bytes a batch of n queries will hold under cfg (slots + pool).
-uint64_t batch_estimate(const gs_graph* g, const gs_batch_config* cfg, uint32_t n,
-                        uint64_t pool_bytes);
+// Does a batch under cfg evaluate plan P in its persistent kernel (else on
+// the grid path)?
+bool batch_in_kernel(const gs_graph* g, const gs_plan* P, const gs_batch_config* cfg);
+// Device bytes a batch under cfg holds whatever its queries: the CTA
+// workspaces of n_kernel kernel queries, and the triple scan's masks when
+// it holds a plan with a scan.
+uint64_t batch_fixed_bytes(const gs_graph* g, const gs_batch_config* cfg, uint32_t n_kernel,
+                           bool has_scan);
 // Non-blocking progress of a batch: *done = 1 once every answer count is
 // known (the grid-path queries it handed on included).
 gs_status batch_advance(gs_batch* b, int* done);
@@ -119,6 +124,21 @@ gs_status result_ready(gs_result* r, int* done);
 // Waits for the result, then moves its answer rows into a right-sized
 // allocation and frees its workspace (fetches read the rows from there).
 gs_status result_compact(gs_result* r);
+
+// Estimated sizes of one evaluation of a plan, from the graph's
+// per-predicate statistics (labels taken as independent of the structure):
+// tree nodes per level, answer rows and the device bytes they take.
+struct Estimate {
+    double nodes[kMaxLevels];
+    double rows;
+    uint64_t arena;      // control block, levels, their scratch, answer rows
+    uint64_t vectors;    // candidate vectors of a plan with a triple scan
+    uint64_t answer;     // answer rows alone
+    uint64_t total;      // arena + vectors (+ the scan's masks for a query alone)
+};
+void plan_estimate(const gs_graph* g, const gs_plan* P, Estimate* e);
+// The first workspace a grid-path evaluation of a plan with estimate e takes.
+uint64_t first_arena_bytes(gs_graph* g, const Estimate& e);
 
 uint64_t host_level_off(const uint64_t* n, int l);
 bool small_eligible(const gs_plan* P);
@@ -132,7 +152,15 @@ gs_status enqueue_small(const gs_plan* P, const ExecDev& E, uint32_t* launches, 
 // vectors are already in E.bits (a triple scan shared with other queries,
 // whose status word `scanned` is); the query runs no scan of its own.
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
-                       cudaStream_t st, int start_level = 0, const uint32_t* scanned = nullptr);
+                       cudaStream_t st, int start_level = 0, const uint32_t* scanned = nullptr,
+                       const Store* so = nullptr, const Store* si = nullptr);
+// Per-query LSpM (gs_lspm.cu): the (predicate, orientation) pairs a plan's
+// evaluation reads; an LSpM's orientation; whether an LSpM holds every pair
+// a plan reads.
+void plan_store_preds(const gs_plan* P, std::vector<uint32_t>* rows, std::vector<uint32_t>* cols);
+const Store* lspm_side(const gs_lspm* L, int dir);
+bool lspm_covers(const gs_lspm* L, const gs_plan* P);
+const gs_graph* lspm_graph(const gs_lspm* L);
 // A grid-path evaluation of a plan whose candidate vectors a shared triple
 // scan writes into `bits` (n_levels vectors of ceil(N/32) words, taken over
 // by the result); its stream waits for `ready` before the first kernel, and

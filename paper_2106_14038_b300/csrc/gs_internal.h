@@ -122,6 +122,10 @@ struct gs_graph {
     // queries whose first level is certainly large away from the
     // single-CTA evaluator
     std::vector<uint32_t> deg_out, deg_in;
+    // per predicate label l and orientation (0 = CSR, 1 = CSC): entries with
+    // label l (lab_cnt) and rows / columns holding it (lab_rows); the
+    // memory estimates of queries are made from these
+    std::vector<uint64_t> lab_cnt[2], lab_rows[2];
     // per-query host resources kept for reuse: timing events and pinned
     // slots the control-block head of a result is copied into
     std::mutex res_mu;
@@ -236,6 +240,9 @@ namespace gs {
 gs_status build_store(gs_graph* g, const uint32_t* s, const uint32_t* p, const uint32_t* o,
                       uint64_t n, bool on_device, cudaStream_t st);
 void free_store(gs_graph* g, cudaStream_t st);
+// The triple scan's work items and row-start bitmap of an orientation whose
+// ptr / idx / lab (M entries) are built; allocated through g's allocator.
+gs_status store_items(const gs_graph* g, Store& S, uint64_t M, cudaStream_t st);
 // radix sort of 64-bit keys on bits [lo_bit, hi_bit); keys end up in *keys
 // (the buffers may be swapped). tmp must hold n keys.
 gs_status radix_sort_u64(const gs_graph* g, uint64_t** keys, uint64_t** tmp, uint64_t n,
@@ -248,8 +255,11 @@ gs_status radix_sort_u64(const gs_graph* g, uint64_t** keys, uint64_t** tmp, uin
 // wide: 32-bit masks (up to kMaxSlotsWide predicates per direction).
 size_t scan_work_bytes(const gs_graph* g, bool wide = false);
 long long scan_stall_cycles();
+// so / si: the orientations to scan (NULL: the graph's own; a per-query
+// LSpM otherwise).
 gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void* work,
-                   cudaStream_t st, uint32_t* status);
+                   cudaStream_t st, uint32_t* status, const Store* so = nullptr,
+                   const Store* si = nullptr);
 
 // One candidate vector to write: vertex x is set when its row mask holds
 // every slot of need_out and its column mask every slot of need_in.
@@ -271,7 +281,7 @@ struct EvalArgs {
 // true) then); scan_eval turns them into the vectors of ea.
 gs_status scan_masks(const gs_graph* g, const uint32_t* out_pred, uint32_t n_out,
                      const uint32_t* in_pred, uint32_t n_in, void* work, uint32_t* status,
-                     cudaStream_t st);
+                     cudaStream_t st, const Store* so = nullptr, const Store* si = nullptr);
 gs_status scan_eval(const gs_graph* g, const void* work, bool wide, const EvalArgs& ea,
                     cudaStream_t st);
 // The ScanSpec of one grouped selection (one candidate vector) from the

@@ -503,28 +503,29 @@ static gs_status allow_smem(int dev, size_t smem) {
 }
 
 template <typename LutT, typename MaskT>
-static gs_status launch_scan(const gs_graph* g, const ScanPreds& sd, void* mask_out, void* mask_in,
-                             uint32_t* status, uint32_t warps, cudaStream_t st) {
+static gs_status launch_scan(const gs_graph* g, const Store& so, const Store& si, const ScanPreds& sd,
+                             void* mask_out, void* mask_in, uint32_t* status, uint32_t warps,
+                             cudaStream_t st) {
     const size_t smem = scan_smem_bytes<LutT, MaskT>(g->P, warps);
     gs_status arc = allow_smem<LutT, MaskT>(g->device, smem);
     if (arc != GS_OK) return arc;
     // one CTA per SM (the shared memory admits no second one)
-    const uint32_t n_items = g->out.n_items + g->in.n_items;
+    const uint32_t n_items = so.n_items + si.n_items;
     const uint32_t grid = std::max(1u, std::min((uint32_t)g->sm_count, (n_items + warps - 1) / warps));
-    const ScanSide out{dview(g->out), g->out.heads, g->out.items, g->out.n_items, mask_out};
-    const ScanSide in{dview(g->in), g->in.heads, g->in.items, g->in.n_items, mask_in};
+    const ScanSide out{dview(so), so.heads, so.items, so.n_items, mask_out};
+    const ScanSide in{dview(si), si.heads, si.items, si.n_items, mask_in};
     GS_CUDA(launch_chained(k_scan<LutT, MaskT>, dim3(grid), dim3(warps * 32), smem, st, out, in,
                            g->N, g->P, sd, status));
     return GS_OK;
 }
 
 template <typename MaskT>
-static gs_status scan_masks_as(const gs_graph* g, const ScanPreds& sd, void* work, uint32_t* status,
-                               cudaStream_t st) {
+static gs_status scan_masks_as(const gs_graph* g, const Store& so, const Store& si,
+                               const ScanPreds& sd, void* work, uint32_t* status, cudaStream_t st) {
     MaskT* mask_out = (MaskT*)work;
     MaskT* mask_in = mask_out + mask_slots(g->N);
-    k_scan_zero<<<g->n_blocks, kThreads, 0, st>>>(g->out.items, g->out.n_items, g->in.items,
-                                                  g->in.n_items, reinterpret_cast<uint32_t*>(mask_out),
+    k_scan_zero<<<g->n_blocks, kThreads, 0, st>>>(so.items, so.n_items, si.items, si.n_items,
+                                                  reinterpret_cast<uint32_t*>(mask_out),
                                                   reinterpret_cast<uint32_t*>(mask_in),
                                                   sizeof(MaskT) == 2 ? 1u : 0u);
     // the one-hot table unless it costs more than a few warps; else the
@@ -532,13 +533,16 @@ static gs_status scan_masks_as(const gs_graph* g, const ScanPreds& sd, void* wor
     using Wide = typename std::conditional<sizeof(MaskT) == 2, uint16_t, uint32_t>::type;
     const uint32_t ww = scan_warps_fit<MaskT>(g->P, sizeof(Wide));
     const uint32_t w8 = scan_warps_fit<MaskT>(g->P, sizeof(uint8_t));
-    if (ww >= 12 || ww >= w8) return launch_scan<Wide, MaskT>(g, sd, mask_out, mask_in, status, ww, st);
-    return launch_scan<uint8_t, MaskT>(g, sd, mask_out, mask_in, status, w8, st);
+    if (ww >= 12 || ww >= w8)
+        return launch_scan<Wide, MaskT>(g, so, si, sd, mask_out, mask_in, status, ww, st);
+    return launch_scan<uint8_t, MaskT>(g, so, si, sd, mask_out, mask_in, status, w8, st);
 }
 
 gs_status scan_masks(const gs_graph* g, const uint32_t* out_pred, uint32_t n_out,
                      const uint32_t* in_pred, uint32_t n_in, void* work, uint32_t* status,
-                     cudaStream_t st) {
+                     cudaStream_t st, const Store* so, const Store* si) {
+    if (!so) so = &g->out;
+    if (!si) si = &g->in;
     if (!status) { set_error("internal: the triple scan needs a status word"); return GS_EINVAL; }
     if (n_out > (uint32_t)kMaxSlotsWide || n_in > (uint32_t)kMaxSlotsWide) {
         set_error("internal: more than %d predicates per direction in one scan", kMaxSlotsWide);
@@ -551,8 +555,8 @@ gs_status scan_masks(const gs_graph* g, const uint32_t* out_pred, uint32_t n_out
     for (uint32_t i = 0; i < n_in; ++i) sd.in_pred[i] = in_pred[i];
     sd.stall_cycles = scan_stall_cycles();
     const bool wide = n_out > (uint32_t)kMaxSlots || n_in > (uint32_t)kMaxSlots;
-    return wide ? scan_masks_as<uint32_t>(g, sd, work, status, st)
-                : scan_masks_as<uint16_t>(g, sd, work, status, st);
+    return wide ? scan_masks_as<uint32_t>(g, *so, *si, sd, work, status, st)
+                : scan_masks_as<uint16_t>(g, *so, *si, sd, work, status, st);
 }
 
 gs_status scan_eval(const gs_graph* g, const void* work, bool wide, const EvalArgs& ea,
@@ -573,9 +577,9 @@ gs_status scan_eval(const gs_graph* g, const void* work, bool wide, const EvalAr
 }
 
 gs_status run_scan(const gs_graph* g, const ScanSpec& spec, uint32_t* bits, void* work,
-                   cudaStream_t st, uint32_t* status) {
+                   cudaStream_t st, uint32_t* status, const Store* so, const Store* si) {
     gs_status rc = scan_masks(g, spec.out_pred, (uint32_t)spec.n_out, spec.in_pred,
-                              (uint32_t)spec.n_in, work, status, st);
+                              (uint32_t)spec.n_in, work, status, st, so, si);
     if (rc != GS_OK) return rc;
     EvalArgs ea{};
     ea.n = (uint32_t)spec.n_bvars;

@@ -1,9 +1,12 @@
 // Serving loop: continuous batching of submitted queries over the resident
 // graph. A worker thread owns the device work:
 //   - admission: queued plans are taken in arrival order into a batch while
-//     the batch's device memory estimate (per-CTA workspace slots plus an
-//     answer pool) fits under the server's budget together with everything
-//     in flight, and while a stream is free;
+//     the batch's estimated device bytes fit under the server's budget
+//     together with everything in flight, and while a stream is free. Each
+//     plan's bytes come from its estimated intermediate results (binding-
+//     tree levels, answers, candidate vectors; gs_plan_estimate); a plan
+//     that does not fit waits and later, smaller ones pass it, until it has
+//     waited long enough that nothing passes it any more;
 //   - launch: the batch runs on its own stream (gs_eval_batch's persistent
 //     kernel), so batches admitted while others are running overlap on the
 //     device;
@@ -16,6 +19,7 @@
 // under one mutex, and CUDA work for one batch is only issued by the worker.
 #include <algorithm>
 #include <chrono>
+#include <functional>
 #include <condition_variable>
 #include <deque>
 #include <memory>
@@ -54,6 +58,13 @@ struct Ticket {
     uint64_t rows = 0;
     gs_status err = GS_OK;
     std::string msg;              // why the query failed
+    // estimated device bytes while its batch runs (from gs_plan_estimate's
+    // model): kernel queries hold a share of the answer pool; grid-path
+    // queries hold their candidate vectors and, while they run, a workspace
+    bool kernel = false, scan = false;
+    uint64_t share = 0;           // pool share (kernel) or first workspace (grid path)
+    uint64_t vectors = 0;         // candidate vectors (plans with a triple scan)
+    uint64_t batch_seq = 0;       // 1-based number of the batch that took it
 };
 
 }  // namespace
@@ -72,15 +83,37 @@ struct gs_server {
     std::vector<std::shared_ptr<Flight>> inflight;
     uint64_t next_id = 1;
     uint64_t inflight_bytes = 0, peak_bytes = 0;
-    uint64_t completed = 0, batches = 0;
+    uint64_t completed = 0, batches = 0, passed = 0;
     gs_status fatal = GS_OK;
 };
 
 namespace {
 
-// Device bytes a batch of n queries will hold while it runs.
-uint64_t estimate(const gs_server* s, uint32_t n) {
-    return batch_estimate(s->g, &s->cfg.batch, n, (uint64_t)n * s->cfg.pool_bytes_per_query);
+// A batch being assembled: the estimated device bytes of the tickets taken.
+struct Admit {
+    uint32_t n_kernel = 0;
+    bool scan = false;
+    uint64_t pool = 0, vectors = 0;
+    std::vector<uint64_t> grid;        // workspaces of its grid-path queries
+};
+
+// Device bytes the batch holds while it runs: fixed CTA workspaces and scan
+// masks, the answer pool, every candidate vector, and the workspaces of the
+// grid_streams largest grid-path queries (they run that many at a time).
+uint64_t admit_bytes(const gs_server* s, const Admit& a) {
+    std::vector<uint64_t> g = a.grid;
+    const size_t k = std::min<size_t>(g.size(), std::max<uint32_t>(1, s->cfg.batch.grid_streams ? s->cfg.batch.grid_streams : 4));
+    std::partial_sort(g.begin(), g.begin() + k, g.end(), std::greater<uint64_t>());
+    uint64_t grid = 0;
+    for (size_t i = 0; i < k; ++i) grid += g[i];
+    return batch_fixed_bytes(s->g, &s->cfg.batch, a.n_kernel, a.scan) + a.pool + a.vectors + grid;
+}
+
+void admit_add(Admit& a, const Ticket& t) {
+    if (t.kernel) { a.n_kernel++; a.pool += t.share; }
+    else a.grid.push_back(t.share);
+    a.scan |= t.scan;
+    a.vectors += t.vectors;
 }
 
 void complete(gs_server* s, std::shared_ptr<Flight>& f, gs_status rc) {
@@ -140,32 +173,55 @@ void worker_loop(gs_server* s) {
                 for (size_t k = 0; k < s->streams.size(); ++k)
                     if (!s->stream_busy[k]) { st = (int)k; break; }
                 if (st < 0) break;
-                uint32_t take = 0;
+                // Tickets in arrival order while the batch's estimated bytes
+                // fit the budget beside everything in flight. One that does
+                // not fit waits and later ones may pass it, unless it has
+                // waited 50 x max_wait_us: then nothing passes it and memory
+                // drains until it fits. A ticket that cannot fit even alone
+                // is admitted alone once nothing else is in flight.
+                Admit a;
+                std::vector<uint64_t> take_ids;
                 uint64_t bytes = 0;
-                while (take < s->queue.size() && take < s->cfg.max_batch) {
-                    uint64_t b2 = estimate(s, take + 1);
-                    if (s->inflight_bytes + b2 > s->cfg.memory_budget && take > 0) break;
-                    bytes = b2;
-                    ++take;
+                const auto now = Clock::now();
+                for (auto it = s->queue.begin(); it != s->queue.end() && take_ids.size() < s->cfg.max_batch;) {
+                    Ticket& t = s->tickets[*it];
+                    Admit a2 = a;
+                    admit_add(a2, t);
+                    const uint64_t b2 = admit_bytes(s, a2);
+                    const bool alone = s->inflight.empty() && take_ids.empty();
+                    if (s->inflight_bytes + b2 <= s->cfg.memory_budget || alone) {
+                        a = a2;
+                        bytes = b2;
+                        take_ids.push_back(*it);
+                        it = s->queue.erase(it);
+                        if (alone && s->inflight_bytes + b2 > s->cfg.memory_budget) break;
+                        continue;
+                    }
+                    if (now - t.submitted >= std::chrono::microseconds(50ull * s->cfg.max_wait_us)) break;
+                    ++it;
                 }
-                if (take == 0 || (s->inflight_bytes + bytes > s->cfg.memory_budget && !s->inflight.empty()))
-                    break;   // wait for memory to free up
+                if (take_ids.empty()) break;   // wait for memory to free up
+                for (uint64_t id : take_ids) {   // tickets taken ahead of older waiting ones
+                    for (uint64_t qid : s->queue)   // ids grow in arrival order
+                        if (qid < id) { s->passed++; break; }
+                }
+                const uint32_t take = (uint32_t)take_ids.size();
                 auto f = std::make_shared<Flight>();
                 f->stream = st;
                 f->bytes = bytes;
+                const uint64_t seq = s->batches + 1;
                 for (uint32_t i = 0; i < take; ++i) {
-                    uint64_t id = s->queue.front();
-                    s->queue.pop_front();
-                    Ticket& t = s->tickets[id];
+                    Ticket& t = s->tickets[take_ids[i]];
                     t.state = 1;
                     t.flight = f;
                     t.index = i;
-                    f->tickets.push_back(id);
+                    t.batch_seq = seq;
+                    f->tickets.push_back(take_ids[i]);
                     f->plans.push_back(t.plan);
                 }
                 f->refs = (int)take;
                 gs_batch_config bc = s->cfg.batch;
-                bc.pool_bytes = s->cfg.pool_bytes_per_query * take;
+                bc.pool_bytes = std::max<uint64_t>(a.pool, 1ull << 20);
                 gs_status rc = eval_batch_ex(s->g, f->plans.data(), take, (void*)s->streams[st],
                                              &bc, 0, &f->b);
                 if (rc != GS_OK) {
@@ -237,24 +293,64 @@ gs_status gs_server_start(gs_graph* g, const gs_server_config* cfg, gs_server** 
     return GS_OK;
 }
 
-gs_status gs_server_submit(gs_server* s, const gs_plan* plan, uint64_t* ticket) {
-    if (!s || !plan || !ticket) { set_error("gs_server_submit: NULL argument"); return GS_EINVAL; }
-    if (plan->N != 0 && (plan->N != s->g->N || plan->P != s->g->P)) {
-        set_error("gs_server_submit: the plan was made for another graph");
-        return GS_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// A queued ticket for plan with its estimated device bytes (filled in
+// outside the lock).
+Ticket make_ticket(gs_server* s, const gs_plan* plan) {
+    Ticket t;
+    Estimate est;
+    plan_estimate(s->g, plan, &est);
+    t.plan = plan;
+    t.kernel = batch_in_kernel(s->g, plan, &s->cfg.batch);
+    t.scan = plan->needs_scan;
+    t.share = t.kernel
+        ? std::min<uint64_t>(std::max<uint64_t>(est.answer + est.answer / 4, 64ull << 10),
+                             s->cfg.pool_bytes_per_query)
+        : first_arena_bytes(s->g, est);
+    t.vectors = est.vectors;
+    return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_server_submit_many(gs_server* s, const gs_plan* const* plans, uint32_t n,
+                                uint64_t* tickets) {
+    if (!s || (n && (!plans || !tickets))) { set_error("gs_server_submit: NULL argument"); return GS_EINVAL; }
+    std::vector<Ticket> ts;
+    ts.reserve(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        const gs_plan* plan = plans[i];
+        if (!plan) { set_error("gs_server_submit: plan %u is NULL", i); return GS_EINVAL; }
+        if (plan->N != 0 && (plan->N != s->g->N || plan->P != s->g->P)) {
+            set_error("gs_server_submit: the plan was made for another graph");
+            return GS_EINVAL;
+        }
+        ts.push_back(make_ticket(s, plan));
     }
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stopping) { set_error("gs_server_submit: the server is stopping"); return GS_EINVAL; }
-        uint64_t id = s->next_id++;
-        Ticket& t = s->tickets[id];
-        t.plan = plan;
-        t.submitted = Clock::now();
-        s->queue.push_back(id);
-        *ticket = id;
+        const auto now = Clock::now();
+        for (uint32_t i = 0; i < n; ++i) {
+            const uint64_t id = s->next_id++;
+            ts[i].submitted = now;
+            s->tickets[id] = ts[i];
+            s->queue.push_back(id);
+            tickets[i] = id;
+        }
     }
     s->cv.notify_one();
     return GS_OK;
+}
+
+gs_status gs_server_submit(gs_server* s, const gs_plan* plan, uint64_t* ticket) {
+    if (!s || !plan || !ticket) { set_error("gs_server_submit: NULL argument"); return GS_EINVAL; }
+    return gs_server_submit_many(s, &plan, 1, ticket);
 }
 
 gs_status gs_server_poll(gs_server* s, uint64_t ticket, int* done, uint64_t* rows,
@@ -309,6 +405,24 @@ gs_status gs_server_release(gs_server* s, uint64_t ticket) {
         if (f && --f->refs > 0) f.reset();
     }
     if (f) gs_free_batch(f->b);   // last ticket of its batch
+    return GS_OK;
+}
+
+gs_status gs_server_ticket(gs_server* s, uint64_t ticket, uint64_t* batch_seq, uint64_t* est_bytes) {
+    if (!s) { set_error("gs_server_ticket: NULL argument"); return GS_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) { set_error("gs_server_ticket: unknown ticket %llu", (unsigned long long)ticket); return GS_EINVAL; }
+    if (batch_seq) *batch_seq = it->second.batch_seq;
+    if (est_bytes) *est_bytes = it->second.share + it->second.vectors;
+    return GS_OK;
+}
+
+gs_status gs_server_admission(gs_server* s, uint64_t* passed, uint64_t* inflight_bytes) {
+    if (!s) { set_error("gs_server_admission: NULL argument"); return GS_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (passed) *passed = s->passed;
+    if (inflight_bytes) *inflight_bytes = s->inflight_bytes;
     return GS_OK;
 }
 

@@ -8,6 +8,7 @@
 // orientation into the triple scan's equal-cost work items.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "gs_device.cuh"
 
@@ -283,7 +284,11 @@ static gs_status build_dir(gs_graph* g, const uint32_t* s, const uint32_t* p, co
     k_uniq_write<<<nb, kThreads, 0, st>>>(keys, n_dev, boff, vb, lb, S.idx, S.lab, S.ptr);
     k_ptr_tail<<<nb, kThreads, 0, st>>>(keys, n, vb, lb, g->N, M, S.ptr);
     GS_CUDA(cudaGetLastError());
+    return store_items(g, S, M, st);
+}
 
+gs_status store_items(const gs_graph* g, Store& S, uint64_t M, cudaStream_t st) {
+    const int nb = g->n_blocks;
     // scan items
     const uint32_t w = 1;   // one cost unit per row end
     const uint64_t cost = (uint64_t)w * g->N + M;
@@ -305,6 +310,56 @@ static gs_status build_dir(gs_graph* g, const uint32_t* s, const uint32_t* p, co
     k_heads<<<nb, kThreads, 0, st>>>(S.ptr, g->N, S.heads);
     GS_CUDA(cudaGetLastError());
     GS_CUDA(cudaStreamSynchronize(st));
+    return GS_OK;
+}
+
+// Per predicate label l of one orientation: cnt[l] = entries with label l,
+// rows[l] = rows holding label l. Rows are sorted by (label, other end), so
+// the entries of (row, l) form one run: a run starts at a row start or
+// where the label changes. Labels of a warp's 32 consecutive entries are
+// aggregated with __match_any_sync (one atomic per distinct label).
+__global__ void k_label_stats(const uint32_t* __restrict__ lab, const uint32_t* __restrict__ heads,
+                              uint64_t M, unsigned long long* __restrict__ cnt,
+                              unsigned long long* __restrict__ rows) {
+    const uint32_t lane = lane_id();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull; base < M;
+         base += stride) {
+        const uint64_t k = base + lane;
+        const bool in = k < M;
+        const uint32_t l = in ? lab[k] : 0xffffffffu;
+        const bool run = in && (((heads[k >> 5] >> (k & 31)) & 1u) || k == 0 || lab[k - 1] != l);
+        const uint32_t same = __match_any_sync(0xffffffffu, l);
+        const uint32_t runs = __ballot_sync(0xffffffffu, run) & same;
+        if (in && lane == (uint32_t)(__ffs(same) - 1)) {
+            atomicAdd(cnt + l, (unsigned long long)__popc(same));
+            if (runs) atomicAdd(rows + l, (unsigned long long)__popc(runs));
+        }
+    }
+}
+
+// Label statistics of both orientations into g->lab_cnt / g->lab_rows.
+static gs_status label_stats(gs_graph* g, cudaStream_t st) {
+    const uint64_t np = (uint64_t)g->P + 1;
+    unsigned long long* d = (unsigned long long*)g->alloc.get(sizeof(unsigned long long) * 4 * np, st);
+    if (!d) { set_error("gs_load_triples: out of device memory for label statistics"); return GS_ENOMEM; }
+    GS_CUDA(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * 4 * np, st));
+    for (int dir = 0; dir < 2; ++dir) {
+        const Store& S = dir ? g->in : g->out;
+        if (g->M) k_label_stats<<<g->n_blocks, kThreads, 0, st>>>(S.lab, S.heads, g->M, d + 2 * dir * np,
+                                                                 d + (2 * dir + 1) * np);
+    }
+    GS_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> h(4 * np);
+    cudaError_t e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * 4 * np,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    g->alloc.put(d, st);
+    if (e != cudaSuccess) return cuda_fail(e, "gs_load_triples (label statistics)");
+    for (int dir = 0; dir < 2; ++dir) {
+        g->lab_cnt[dir].assign(h.begin() + 2 * dir * np, h.begin() + (2 * dir + 1) * np);
+        g->lab_rows[dir].assign(h.begin() + (2 * dir + 1) * np, h.begin() + (2 * dir + 2) * np);
+    }
     return GS_OK;
 }
 
@@ -336,6 +391,7 @@ gs_status build_store(gs_graph* g, const uint32_t* s, const uint32_t* p, const u
     if (!k0 || !k1 || !misc) { set_error("gs_load_triples: out of device memory for sort keys"); rc = GS_ENOMEM; }
     if (rc == GS_OK) rc = build_dir(g, ds, dp, dpo, n, 0, vb, lb, k0, k1, misc, g->out, st);
     if (rc == GS_OK) rc = build_dir(g, ds, dp, dpo, n, 1, vb, lb, k0, k1, misc, g->in, st);
+    if (rc == GS_OK) rc = label_stats(g, st);
     g->alloc.put(k0, st);
     g->alloc.put(k1, st);
     g->alloc.put(misc, st);

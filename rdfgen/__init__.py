@@ -391,37 +391,49 @@ def bandwidth_root(shape: Shape) -> int:
     return max(range(shape.n_v), key=lambda v: (deg[v], -v))
 
 
+def rare_cycle(k: int, pendant: bool = False) -> Shape:
+    """A k-cycle on vertices 0..k-1 laid out for the bandwidth workload: the
+    tree is the path 0, k-1, k-2, .., 1 (its edges take rare predicates),
+    the closing edge (1, 0) is the non-tree edge (it takes one of the most
+    frequent predicates). With pendant, vertex k hangs on vertex 0 by one
+    more rare edge."""
+    e = [(0, k - 1)] + [(i, i - 1) for i in range(k - 1, 1, -1)]
+    if pendant:
+        e.append((0, k))
+    e.append((1, 0))
+    return Shape("cycle%d%s" % (k, "+leaf" if pendant else ""), k + (1 if pendant else 0), e,
+                 k - 1 + (1 if pendant else 0))
+
+
 def _shapes_bandwidth(w: Workload, n: int):
-    """Constant-free cycles whose first evaluated group (the root's incident
-    edges) takes predicates among the 8 most frequent, so the root's
-    candidate set is large and its expansion reads many edges, while every
-    edge off the root and the pendant edge take predicates from the rarer
-    half (ids above P/2), which keeps the answer small. In turn: 4-cycle,
-    4-cycle with a pendant vertex on the root, 3-cycle, 5-cycle."""
+    """Constant-free cycles, in turn: 3-cycle, 4-cycle, 3-cycle with a
+    pendant edge on the root, 4-cycle with one. The root (vertex 0, where
+    the degree-driven traversal starts) is evaluated first with all its
+    edges together (Sec. 5): its closing edge takes one of the 8 most
+    frequent predicates, so expanding it from the root's candidates reads
+    long ranges of a frequent predicate; every other edge takes a predicate
+    from the rarer half (ids above P/2), so the answer stays small."""
     top = (1, 8)
     tail = (w.n_preds // 2 + 1, w.n_preds)
     out = []
     for q in range(n):
         kind = q % 4
-        sh = cycle(4) if kind == 0 else cycle_leaf(4) if kind == 1 else cycle(3) if kind == 2 \
-            else cycle(5)
-        root = bandwidth_root(sh)
-        ring = sh.n_v - (1 if kind == 1 else 0)          # vertices on the cycle
-        for e, (u, v) in enumerate(sh.edges):
-            on_ring = u < ring and v < ring
-            sh.pred_range[e] = top if on_ring and root in (u, v) else tail
+        sh = rare_cycle(3 if kind in (0, 2) else 4, pendant=kind >= 2)
+        for e in range(len(sh.edges)):
+            sh.pred_range[e] = top if e == len(sh.edges) - 1 else tail
+        assert bandwidth_root(sh) == 0
         out.append(sh)
     return out
 
 
 def bandwidth_queries(w: Workload, sampler: Sampler, n: int | None = None,
-                      cap: float | None = None, attempts: int = 4000):
-    """The bandwidth-bound workload: constant-free cycles (see
-    _shapes_bandwidth), each the first seeded embedding whose spanning-tree
-    bound (the path through the root's first edge, the rare edges and the
-    pendant edge) is at most cap, so its exact answer count is at most cap.
-    Every query has at least its embedding as an answer. Bounds depend only
-    on the predicates and directions and are cached on them."""
+                      cap: float | None = None, attempts: int = 2000):
+    """The bandwidth-bound workload: for shape q (see _shapes_bandwidth),
+    its first seeded embedding whose spanning-tree bound is at most cap.
+    The tree holds every edge but the frequent closing one, so the bound
+    (the match count of the rare path) caps the exact answer count. Every
+    query has at least its embedding as an answer. Bounds depend only on
+    the predicates and directions and are cached on them."""
     cap = w.cap if cap is None else cap
     shapes = _shapes_bandwidth(w, w.n_queries if n is None else n)
     cache = {}
@@ -432,7 +444,7 @@ def bandwidth_queries(w: Workload, sampler: Sampler, n: int | None = None,
             q = sampler.embed(sh, w.query_seed, qi * 100003 + a, with_bound=False)
             if q is None:
                 continue
-            key = (tuple(q.patterns[:, 1].tolist()), tuple(q.u_subject.tolist()))
+            key = (tuple(q.patterns[:-1, 1].tolist()), tuple(q.u_subject[:-1].tolist()))
             if key not in cache:
                 cache[key] = sampler.tree_bound(sh, q)
             q.bound = cache[key]
@@ -443,6 +455,31 @@ def bandwidth_queries(w: Workload, sampler: Sampler, n: int | None = None,
             raise RuntimeError("no embedding of %s within bound %g in %d attempts"
                                % (sh.name, cap, attempts))
         out.append(got)
+    return out
+
+
+def save_queries(path: str, qs, header: str = ""):
+    """Write queries as text: per query one line 'shape bound n s p o ...'."""
+    with open(path, "w") as f:
+        for line in header.splitlines():
+            f.write("# %s\n" % line)
+        for q in qs:
+            f.write("%s %.6g %d %s\n" % (q.shape, q.bound, len(q.patterns),
+                                         " ".join(str(int(x)) for x in q.patterns.reshape(-1))))
+
+
+def load_queries(path: str):
+    """Queries written by save_queries (embedding unknown: all zero)."""
+    out = []
+    with open(path) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            t = line.split()
+            n = int(t[2])
+            pat = np.array([int(x) for x in t[3:3 + 3 * n]], np.int64).reshape(n, 3)
+            k = int(-pat[:, [0, 2]][pat[:, [0, 2]] < 0].min())
+            out.append(Query(pat, k, t[0], float(t[1]), np.zeros(0, np.uint32)))
     return out
 
 

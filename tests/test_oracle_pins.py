@@ -264,3 +264,33 @@ def test_invariants(seed):
         extra = np.array([[pats[0][0], 1 + seed % w.n_preds, pats[-1][2]]], np.int64)
         sub = ix.eval(np.concatenate([pats, extra]))
         assert set(map(tuple, sub.tolist())) <= set(map(tuple, base.tolist()))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_count_mode_equals_row_count(seed):
+    """The count mode walks the same join without storing rows: its count is
+    the number of rows eval returns, on any thread count; a step limit below
+    the join's work is reported as incomplete with a lower bound."""
+    s, p, o = rdfgen.random_graph(seed + 40, 40, 3, 400)
+    ix = oracle.Index(s, p, o, 40, 3)
+    for q in range(30):
+        pat = rdfgen.random_bgp(seed * 1000 + q, 40, 3, max_vars=4, max_patterns=4)
+        rows = ix.eval(pat)
+        for t in (1, 3):
+            n, steps, done = ix.count(pat, threads=t)
+            assert done and n == len(rows)
+        n, steps, done = ix.count(pat)
+        if steps > 4:
+            m, _, done2 = ix.count(pat, max_steps=2)
+            assert not done2 and m <= n
+
+
+def test_index_sorted_copies_are_sorted_and_deduplicated():
+    """The bucket-sorted copies hold the set of triples, each in its order."""
+    s, p, o = rdfgen.random_graph(9, 300, 5, 20000)
+    ix = oracle.Index(s, p, o, 300, 5)
+    want = sorted(set(zip(s.tolist(), p.tolist(), o.tolist())))
+    ts, tp, to = ix.triples()
+    assert list(zip(ts.tolist(), tp.tolist(), to.tolist())) == want
+    bs, bp, bo = ix.triples(by_object=True)
+    assert list(zip(bo.tolist(), bp.tolist(), bs.tolist())) == sorted((c, b, a) for a, b, c in want)

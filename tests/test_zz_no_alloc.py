@@ -58,9 +58,13 @@ def test_noalloc_matches_scan_on_consecutive_calls():
     want = [g.scan(pr, dr, stream=stream) for g, (pr, dr) in pairs]
     outs = [torch.full(((g.n_vertices + 31) // 32,), -1, dtype=torch.int32, device="cuda")
             for g, _ in pairs]
+    import gc
+    gc.collect()                 # earlier tests' garbage is freed before the baseline
     torch.cuda.synchronize()
     calls, live = alloc.calls, dict(alloc.live)
-    used = torch.cuda.memory_allocated()
+    # cumulative count of the caching allocator's allocations: frees of
+    # unrelated tensors do not move it, any allocation does
+    made = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
     # back to back on one stream, alternating graphs so each call starts on
     # the previous call's leftovers in the static workspace
     for (g, (pr, dr)), out in zip(pairs, outs):
@@ -69,7 +73,7 @@ def test_noalloc_matches_scan_on_consecutive_calls():
         g.scan_noalloc(pr, dr, out, stream=stream)
     torch.cuda.synchronize()
     assert alloc.calls == calls and alloc.live == live
-    assert torch.cuda.memory_allocated() == used
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == made
     for (g, (pr, dr)), a, b in zip(pairs, want, outs):
         assert torch.equal(a, b), (g.n_vertices, pr, dr)
     big.scan_status()
