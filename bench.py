@@ -1,16 +1,20 @@
-"""Benchmark: BGP queries/s (plain form, one query at a time) on a seeded
-R-MAT RDF graph resident on one B300, with p50/p99 latency, the triple-scan
-roofline and the CPU oracle beside it. Prints one JSON line on rank 0.
+"""Benchmark: BGP queries/s with p50/p99 latency on seeded R-MAT RDF graphs
+resident on one B300, the triple-scan roofline and the CPU oracle beside
+them. Prints one JSON line on rank 0.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat22]
-                    [--impl gsmart|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat26]
+                    [--impl gsmart|reference] [--mode plain|scan|batched|served|query]
 
-A step evaluates every query of the workload once, one after another:
-plan on the host, evaluate on the device, wait for the answer count (the
-answer rows stay on the device). `e2e` is the same step through the public
-API with the answer rows fetched into pinned host memory. With N > 1
+Default (the scale-26, 1.07e9-triple graph): the bandwidth workload's
+constant-free cycles, each of which starts with a triple scan over all
+2.1e9 labels. The headline is served queries/s under Poisson arrivals at
+20,000 offered queries/s (a step is 256 arrivals); the same queries one at
+a time (plain) and as one batch are reported beside it, and `e2e` is the
+served replay with every answer copied into pinned host memory.
+`--workload rmat22` is the mid configuration: its 32 mixed queries one at
+a time per step, with the answer rows fetched for `e2e`. With N > 1
 (torchrun) every rank holds its own copy of the graph and runs the whole
-query list (replicas: queries are independent, there is no exchange).
+workload (replicas: queries are independent, there is no exchange).
 """
 from __future__ import annotations
 
@@ -36,7 +40,7 @@ def _args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="rmat22")
+    ap.add_argument("--workload", default="rmat26")
     ap.add_argument("--impl", default="gsmart", choices=["gsmart", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the CPU oracle sample")
@@ -53,6 +57,8 @@ def _args():
                     help="batched mode: number of queries (0: the workload's)")
     ap.add_argument("--query", default="0",
                     help="query mode: comma-separated indices into the workload's queries")
+    ap.add_argument("--batch", action="store_true",
+                    help="query mode: evaluate the selected queries as one batch per round")
     return ap.parse_args()
 
 
@@ -148,10 +154,32 @@ def _dist():
 def _workload(name):
     w = rdfgen.WORKLOADS[name]
     s, p, o = rdfgen.graph(w)
+    if name == "rmat26":     # the bandwidth workload's stored queries
+        return w, (s, p, o), rdfgen.bandwidth_workload(w)
     sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
     qs = rdfgen.queries(w, sm)
     sm.close()
     return w, (s, p, o), qs
+
+
+BANDWIDTH_METRIC = ("BGP queries/s (served: Poisson arrivals, continuous batching; plain and "
+                    "batched beside), triple-scan HBM GB/s")
+PER_STEP = 256           # arrivals per step of the served headline
+TOP_RATE = 20000         # its offered queries/s
+
+
+def _bandwidth_config(w, M, n_queries, ws):
+    """config of the scale-26 line, the same for both arms."""
+    N = w.n_vertices
+    return {"workload": w.name, "scale": w.scale, "triples_drawn": w.n_edges, "triples": int(M),
+            "predicates": w.n_preds, "queries": n_queries,
+            "query_mix": "constant-free 3-/4-cycles, with and without a pendant edge "
+                         "(rdfgen/rmat26_bandwidth.txt)",
+            "offered_qps": TOP_RATE, "arrivals_per_step": PER_STEP,
+            "memory_budget_bytes": 40 << 30,
+            "l2": "inputs larger than L2 (graph %.1f GB; every query scans 2.1e9 labels)"
+                  % ((8 * (N + 1) + 16 * M) / 1e9),
+            "parallelism": "replicas" if ws > 1 else "single"}
 
 
 def _cpu_baseline(w, triples, qs, budget_s):
@@ -201,13 +229,18 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = args.steps * len(sample) / dt
     desc = "first %d of %d queries of %s per step" % (len(sample), len(qs), w.name)
+    if w.name == "rmat26":
+        metric, config = BANDWIDTH_METRIC, _bandwidth_config(w, len(ix), len(qs), ws)
+    else:
+        metric = "BGP queries/s (plain, one at a time)"
+        config = {"workload": w.name, "scale": w.scale, "triples_drawn": w.n_edges,
+                  "predicates": w.n_preds, "queries": len(qs)}
     print(json.dumps({
-        "impl": "reference", "metric": "BGP queries/s (plain, one at a time)", "value": v,
+        "impl": "reference", "metric": metric, "value": v,
         "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": w.name, "scale": w.scale, "triples_drawn": w.n_edges,
-                   "predicates": w.n_preds, "queries": len(qs)},
+        "config": config,
         "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -408,7 +441,8 @@ def run_gsmart(args):
 # sha1 prefix of the scan source the counters were taken on; the summary is
 # in profiles/. A changed kernel reports null until it is captured again.
 SCAN_TRAFFIC = {
-    "rmat22": ("660d2fbd38d7", 617214464),
+    "rmat22": ("52b3e7feb70b", 617061632),
+    "rmat26": ("52b3e7feb70b", 10649042944),
 }
 
 
@@ -660,6 +694,25 @@ def run_query(args):
     g = gs.Graph(*triples, w.n_vertices, w.n_preds)
     sel = [int(x) for x in args.query.split(",")]
     stream = torch.cuda.current_stream()
+    if args.batch:
+        plans = [g.plan(qs[i].patterns) for i in sel]
+        ms, launches = [], 0
+        for rep in range(args.warmup + args.steps):
+            b = g.eval_batch(plans, stream)
+            rows = b.rows()
+            st = b.stats()
+            if rep >= args.warmup:
+                ms.append(st[0])
+                launches += st[1]
+            scans = b.scans()
+            b.close()
+        print(json.dumps({
+            "metric": "device ms per batch", "unit": "ms", "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": w.name, "queries": sel}, "device_ms": float(np.mean(ms)),
+            "rows": [int(x) for x in rows], "triple_scans": scans[0], "gpu_launches": launches,
+        }), flush=True)
+        return
     dev = {i: [] for i in sel}
     info = {}
     launches = 0
@@ -685,8 +738,214 @@ def run_query(args):
     }), flush=True)
 
 
+def run_bandwidth(args):
+    """The bandwidth-bound configuration (the default line): the scale-26
+    graph resident; the constant-free cycles of rdfgen/rmat26_bandwidth.txt,
+    each starting with a triple scan over all 2.1e9 labels. Headline: served
+    q/s under Poisson arrivals at the top offered rate (a step = 256
+    arrivals), with p50/p99; beside it the lower offered rates, the same
+    queries one at a time (plain) and as one batch, the end-to-end replay
+    with every answer fetched into pinned host memory, the triple-scan
+    roofline and the oracle on the host cores."""
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    import paper_2106_14038_b300 as gs
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = rdfgen.WORKLOADS[args.workload]
+    t_setup = time.perf_counter()
+    triples = rdfgen.graph(w)
+    g = gs.Graph(*triples, w.n_vertices, w.n_preds)
+    qs = rdfgen.bandwidth_workload(w)
+    plans = [g.plan(q.patterns) for q in qs]
+    setup_s = time.perf_counter() - t_setup
+    stream = torch.cuda.current_stream()
+    N, M = w.n_vertices, g.n_triples
+
+    # plain: one query at a time (plan + evaluation + answer count)
+    def plain_pass(lat=None):
+        nl = 0
+        for q in qs:
+            t0 = time.perf_counter()
+            plan = g.plan(q.patterns)
+            r = g.eval(plan, stream)
+            r.info()
+            if lat is not None:
+                lat.append(time.perf_counter() - t0)
+            nl += r.stats()[1]
+            r.close()
+            plan.close()
+        return nl
+    for _ in range(args.warmup):
+        plain_pass()
+    lat, pl_ms = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        plain_pass(lat)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        pl_ms.append(ev0.elapsed_time(ev1))
+    plain_q, _ = aggregate_rate(float(np.sum(pl_ms)), len(qs) * args.steps, ws, dist)
+    lat_ms = 1000 * np.array(lat)
+    rows = [int(g.eval(pl, stream).info()[0]) for pl in plans]
+
+    # batched: all queries in one launch per step, autotuned on them
+    bcfg, tune_ms = g.autotune_batch(plans, stream)
+    b_ms, b_scans = [], None
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = g.eval_batch(plans, stream, config=bcfg)
+        b.rows()
+        if i >= args.warmup:
+            b_ms.append(1000 * (time.perf_counter() - t0))
+            b_scans = b.scans()
+        b.close()
+    b_q, _ = aggregate_rate(float(np.sum(b_ms)), len(qs) * args.steps, ws, dist)
+
+    # served: Poisson arrivals; the top rate is the headline, K steps of
+    # PER_STEP arrivals (fewer when the batched capacity says the run would
+    # pass about 90 s; the line then states its arrivals_per_step)
+    cap_qps = max(b_q, plain_q)
+    per_step = int(min(PER_STEP, max(16, 90.0 * cap_qps / max(1, args.steps + args.warmup))))
+    rates = [200, 2000, TOP_RATE]
+    served = []
+    peaks, which = _peaks()
+    srv_cfg = dict(batch=bcfg)
+    for rate in rates[:-1]:
+        n = int(min(max(100, rate), max(50, 20.0 * cap_qps)))
+        sched = np.cumsum(np.random.default_rng(5000 + rate).exponential(1.0 / rate, n))
+        srv = gs.Server(g, **srv_cfg)
+        lat_us, done_s = srv.replay(plans, sched)
+        served.append(_served_entry(srv, rate, n, sched, lat_us, done_s))
+        srv.stop()
+    top = rates[-1]
+    srv = gs.Server(g, **srv_cfg)
+    warm = np.cumsum(np.random.default_rng(6000).exponential(1.0 / top, per_step * args.warmup))
+    srv.replay(plans, warm)
+    n = per_step * args.steps
+    sched = np.cumsum(np.random.default_rng(6001).exponential(1.0 / top, n))
+    l0 = srv.work()[0]
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        lat_us, done_s = srv.replay(plans, sched)
+        torch.cuda.synchronize()
+    barrier()
+    launches = srv.work()[0] - l0
+    head = _served_entry(srv, top, n, sched, lat_us, done_s)
+    served.append(head)
+    srv.stop()
+    span_ms = 1000.0 * float(done_s.max() - sched[0])
+    value, t_ms = aggregate_rate(span_ms, n, ws, dist)
+
+    # end to end: the same replay with every answer fetched into pinned host memory
+    k = max(pl.n_vars for pl in plans)
+    pin = torch.empty(max(rows) * k + 16, dtype=torch.int32, pin_memory=True).numpy()
+    srv = gs.Server(g, **srv_cfg)
+    srv.replay(plans, warm[:per_step], fetch_into=pin)
+    lat_e, done_e, fetched = srv.replay(plans, sched, fetch_into=pin)
+    srv.stop()
+    e2e_value, _ = aggregate_rate(1000.0 * float(done_e.max() - sched[0]), n, ws, dist)
+    h2d = int(sum(qs[i % len(qs)].patterns.nbytes for i in range(per_step)))
+
+    # the triple scan over the whole matrix (the bandwidth kernel)
+    roof = _scan_roofline(g, w, stream, peaks, which)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = _cpu_baseline(w, triples, qs, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps({
+            "metric": BANDWIDTH_METRIC,
+            "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(_bandwidth_config(w, M, len(qs), ws), arrivals_per_step=per_step),
+            "setup_s": setup_s,
+            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
+            "served": served,
+            "plain": {"value": plain_q, "unit": "queries/s",
+                      "p50_ms": float(np.percentile(lat_ms, 50)),
+                      "p99_ms": float(np.percentile(lat_ms, 99)),
+                      "timing": "CUDA events around each pass of the queries, one at a time"},
+            "batched": {"value": b_q, "unit": "queries/s", "ms_per_step": float(np.mean(b_ms)),
+                        "config": bcfg.as_dict(), "autotune_best_ms": tune_ms,
+                        "triple_scans_per_step": b_scans[0], "scan_plans_per_step": b_scans[1],
+                        "timing": "host wall clock per batch (plan + launch + counts)"},
+            "answer_rows": rows,
+            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": int(fetched // max(1, args.steps)),
+                    "path": "gs_server_replay with every answer copied to pinned host memory"},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "gpu_launches": launches,
+        }), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _served_entry(srv, rate, n, sched, lat_us, done_s):
+    completed, batches, peak = srv.stats()
+    launches, scans, scan_plans = srv.work()
+    span = float(done_s.max() - sched[0])
+    return {"offered_qps": rate, "queries": n, "achieved_qps": n / span,
+            "p50_ms": float(np.percentile(lat_us, 50) / 1e3),
+            "p99_ms": float(np.percentile(lat_us, 99) / 1e3),
+            "batches": batches, "queries_per_batch": n / max(1, batches),
+            "triple_scans": scans, "plans_per_scan": scan_plans / max(1, scans),
+            "peak_admitted_bytes": peak}
+
+
+def _scan_roofline(g, w, stream, peaks, which, n_scan=20):
+    """The triple-scan call (Eq. 17 / Eq. 21 over the whole matrix) timed
+    alone with CUDA events: algorithmic bytes 2 (4 (N + 1) + 4 M) + N / 8."""
+    import torch
+    preds, dirs = [1, 2, 3, 1, 2], [0, 0, 0, 1, 1]
+    words = (w.n_vertices + 31) // 32
+    out = torch.empty(words, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        g.scan(preds, dirs, out=out)
+    se0, se1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(n_scan):
+        flush.fill_(1)
+        torch.cuda._sleep(400000)   # ~0.2 ms on the device: the host enqueues the scan meanwhile
+        se0.record(stream)
+        g.scan(preds, dirs, out=out)
+        se1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(se0.elapsed_time(se1))
+    g.scan_status()
+    scan_ms = float(np.mean(ms))
+    N, M = w.n_vertices, g.n_triples
+    alg = 2 * (4 * (N + 1) + 4 * M) + N // 8
+    achieved = alg / (scan_ms / 1000.0) / 1e9
+    return {"kernel": "triple-scan call (gs_scan_candidates: k_scan_zero + k_scan over both "
+                      "orientations + k_scan_eval)",
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_source": which,
+            "traffic": _scan_traffic(w.name), "algorithmic_bytes": alg, "ms_per_launch": scan_ms,
+            "ms_median": float(np.median(ms))}
+
+
 def main():
     args = _args()
+    if args.impl == "gsmart" and args.mode == "plain" and args.workload == "rmat26":
+        run_bandwidth(args)
+        return
     if args.mode == "query" and args.impl == "gsmart":
         run_query(args)
         return

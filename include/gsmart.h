@@ -354,11 +354,19 @@ void gs_server_stop(gs_server* s);
  * and releases them as they finish. latency_us[i] (may be NULL) receives
  * the time from the scheduled arrival to completion as the server's worker
  * saw it, done_s[i] (may be NULL) the completion time since the call
- * started. Returns when every query has finished; GS_ETIMEOUT if that
- * takes longer than timeout_s; a failed query's status otherwise. */
+ * started. With fetch_buf (host memory of fetch_cap_rows rows of the
+ * widest plan; may be NULL) every finished query's answers are copied
+ * there before its release, and *fetched_bytes (may be NULL) gets their
+ * total. Returns when every query has finished; GS_ETIMEOUT if that takes
+ * longer than timeout_s; GS_EOVERFLOW when an answer does not fit
+ * fetch_buf; a failed query's status otherwise. */
 gs_status gs_server_replay(gs_server* s, const gs_plan* const* plans, uint32_t n_plans,
                            const double* arrival_s, uint64_t n, double timeout_s,
-                           double* latency_us, double* done_s);
+                           double* latency_us, double* done_s, int32_t* fetch_buf,
+                           uint64_t fetch_cap_rows, uint64_t* fetched_bytes);
+/* Kernel launches, triple scans and plans served by those scans, summed
+ * over the batches completed so far. Any out pointer may be NULL. */
+gs_status gs_server_work(gs_server* s, uint64_t* launches, uint64_t* scans, uint64_t* scan_plans);
 
 /* ------------------------------------------------------------------ */
 /* One grouped predicate selection on its own (Eq. 17, Eq. 21):

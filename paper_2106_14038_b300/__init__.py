@@ -37,7 +37,7 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_batch_autotune", "gs_server_replay", "gs_scan_status", "gs_batch_scans",
             "gs_plan_estimate", "gs_server_ticket", "gs_server_admission",
             "gs_server_submit_many", "gs_lspm_build", "gs_lspm_for_plan", "gs_lspm_info",
-            "gs_lspm_export", "gs_eval_query_lspm", "gs_free_lspm"]
+            "gs_lspm_export", "gs_eval_query_lspm", "gs_free_lspm", "gs_server_work"]
 
 
 class GsError(RuntimeError):
@@ -141,7 +141,8 @@ def load_library(path: str | None = None):
         "gs_eval_batch": [vp, vp, u32, vp, P(vp)],
         "gs_eval_batch_cfg": [vp, vp, u32, vp, vp, P(vp)],
         "gs_batch_autotune": [vp, vp, u32, vp, vp, P(ctypes.c_float)],
-        "gs_server_replay": [vp, vp, u32, vp, u64, ctypes.c_double, vp, vp],
+        "gs_server_replay": [vp, vp, u32, vp, u64, ctypes.c_double, vp, vp, vp, u64, P(u64)],
+        "gs_server_work": [vp, P(u64), P(u64), P(u64)],
         "gs_batch_info": [vp, vp, P(u64)],
         "gs_batch_fetch": [vp, u32, vp, u64, i32, i32],
         "gs_batch_stats": [vp, P(ctypes.c_float), P(u32), P(u32)],
@@ -598,17 +599,35 @@ class Server:
         _check(_lib.gs_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return int(a.value), int(b.value), int(c.value)
 
-    def replay(self, plans, arrival_s, timeout_s: float = 120.0):
+    def replay(self, plans, arrival_s, timeout_s: float = 120.0, fetch_into=None):
         """Native load replay: query i is plans[i % len(plans)], submitted at
-        arrival_s[i] seconds; returns (latency_us, done_s) arrays."""
+        arrival_s[i] seconds; returns (latency_us, done_s) arrays. With
+        fetch_into (a host int32 array, e.g. pinned torch memory as numpy)
+        every answer is copied there before release; then returns
+        (latency_us, done_s, fetched_bytes)."""
         arr = (ctypes.c_void_p * max(1, len(plans)))(*[p._h.value for p in plans])
         at = np.ascontiguousarray(arrival_s, dtype=np.float64)
         lat = np.zeros(len(at))
         done = np.zeros(len(at))
+        fb = ctypes.c_uint64()
+        buf, cap = None, 0
+        if fetch_into is not None:
+            k = max(p.n_vars for p in plans)
+            buf, cap = fetch_into.ctypes.data_as(ctypes.c_void_p), fetch_into.size // max(k, 1)
         _check(_lib.gs_server_replay(self._h, arr, len(plans), at.ctypes.data_as(ctypes.c_void_p),
                                      len(at), float(timeout_s), lat.ctypes.data_as(ctypes.c_void_p),
-                                     done.ctypes.data_as(ctypes.c_void_p)))
+                                     done.ctypes.data_as(ctypes.c_void_p), buf, cap,
+                                     ctypes.byref(fb)))
+        if fetch_into is not None:
+            return lat, done, int(fb.value)
         return lat, done
+
+    def work(self):
+        """(kernel launches, triple scans, plans those scans served) of the
+        completed batches."""
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib.gs_server_work(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return int(a.value), int(b.value), int(c.value)
 
     def stop(self):
         if getattr(self, "_h", None):

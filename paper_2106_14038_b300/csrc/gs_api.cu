@@ -136,6 +136,8 @@ void give_host_res(gs_graph* g, const cudaEvent_t ev[3], uint8_t* head) {
 constexpr uint64_t kArenaMin = 64ull << 20;
 constexpr uint64_t kArenaDefault = 512ull << 20;
 constexpr uint64_t kSmallRoute = 8192;          // first-level bound above which a query goes straight to the grid path
+constexpr double kSmallNodes = 4096.0;          // estimated level nodes above which it does too (4 x the CTA's budget)
+constexpr double kSmallRows = 16384.0;          // estimated answer rows above which it does too (4 x the CTA's budget)
 constexpr int kMaxRetries = 16;
 
 ExecDev exec_view(gs_result* r) {
@@ -580,13 +582,16 @@ gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, i
         if (!r->lists) { set_error("gs_eval_query: out of device memory"); rc = GS_ENOMEM; }
     }
     // the single-CTA evaluator unless the first level is certainly past its
-    // budget (then it would only hand the query back)
-    r->mode = (small_eligible(plan) && !force_grid && first_level_bound(g, plan) <= kSmallRoute) ? 1 : 0;
+    // budget, or the plan's estimate puts a level or the answer well past
+    // it (then it would most likely hand the query back, a host round trip)
+    Estimate est{};
+    plan_estimate(g, plan, &est);
+    bool big = est.rows > kSmallRows;
+    for (int l = 0; l < plan->n_levels; ++l) big |= est.nodes[l] > kSmallNodes;
+    r->mode = (small_eligible(plan) && !force_grid && !big && first_level_bound(g, plan) <= kSmallRoute) ? 1 : 0;
     if (rc == GS_OK) {
         // the grid path's size for both: a query the single-CTA kernel hands
         // back continues in this workspace
-        Estimate est;
-        plan_estimate(g, plan, &est);
         const uint64_t want = first_arena_bytes(g, est);
         r->arena = (uint8_t*)g->alloc.get(want, r->st);
         r->arena_bytes = want;

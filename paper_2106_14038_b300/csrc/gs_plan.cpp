@@ -12,9 +12,10 @@
 // group; with constants, when no unvisited vertex next to a constant is
 // left, the root is chosen by the rule without constants.
 //
-// Schedule. Variables are materialized in the order the groups reach them
-// (a group's own vertex, then the new ends of its edges): one tree level
-// per variable (Sec. 7.1, one path through all groups). A variable's
+// Schedule. One tree level per variable (Sec. 7.1, one path through all
+// groups). Without a graph, variables are materialized in the order the
+// groups reach them (a group's own vertex, then the new ends of its edges);
+// with one, after the first level, by estimated candidates (greedy_levels). A variable's
 // "binders" are its patterns to constants and to variables of earlier
 // levels; each tree node takes its candidates from the shortest binder
 // range and tests the others by membership. Its patterns to variables of
@@ -187,6 +188,64 @@ void direction_driven(const QGraph& G, Groups& groups, std::vector<int>& roots) 
 
 }  // namespace
 
+// Level order by estimated candidates. The first level stays the
+// traversal's (the root, or the variable its first constant binds); then,
+// repeatedly, the variable whose cheapest edge to a bound end (an earlier
+// level or a constant) has the shortest mean range, from the graph's label
+// statistics: a variable reachable only through frequent predicates waits
+// until a rarer edge binds it, which keeps the binding tree small (its
+// frequent edge becomes a membership test). Ties keep the traversal order;
+// a variable with no edge to a bound end (another component) comes when
+// nothing else is left. The answers do not depend on the order.
+void greedy_levels(const gs_graph* g, const int64_t* pat, uint32_t n, std::vector<int>* order) {
+    const std::vector<int> trav = *order;
+    const double M = std::max<double>(1.0, (double)g->M);
+    auto stat = [&](const std::vector<uint64_t>& v, uint32_t p) { return p < v.size() ? (double)v[p] : 0.0; };
+    // mean range of label p in the row (dir 0) or column (dir 1) of a bound end
+    auto fanout = [&](uint32_t p, int dir) {
+        const double r = stat(g->lab_rows[dir], p);
+        return r > 0 ? stat(g->lab_cnt[dir], p) / r : 0.0;
+    };
+    auto from_const = [&](uint32_t c, uint32_t p, int dir) {
+        const std::vector<uint32_t>& deg = dir == 0 ? g->deg_out : g->deg_in;
+        return c < deg.size() ? deg[c] * stat(g->lab_cnt[dir], p) / M : 0.0;
+    };
+    auto var_of = [](int64_t x) { return x < 0 ? (int)(-x - 1) : -1; };
+    int k = 0;
+    for (int v : trav) k = std::max(k, v + 1);
+    std::vector<char> done(k, 0);
+    std::vector<int> out{trav[0]};
+    done[trav[0]] = 1;
+    while (out.size() < trav.size()) {
+        int best = -1;
+        double best_f = 0.0;
+        for (int v : trav) {
+            if (done[v]) continue;
+            double f = 1e300;
+            for (uint32_t i = 0; i < n; ++i) {
+                const int a = var_of(pat[3 * i]), b = var_of(pat[3 * i + 2]);
+                const uint32_t p = (uint32_t)pat[3 * i + 1];
+                if (a == v && b != v) {   // v the subject: candidates in the object's column
+                    if (b < 0) f = std::min(f, from_const((uint32_t)pat[3 * i + 2], p, 1));
+                    else if (done[b]) f = std::min(f, fanout(p, 1));
+                }
+                if (b == v && a != v) {   // v the object: candidates in the subject's row
+                    if (a < 0) f = std::min(f, from_const((uint32_t)pat[3 * i], p, 0));
+                    else if (done[a]) f = std::min(f, fanout(p, 0));
+                }
+            }
+            if (f >= 1e300) continue;
+            if (best < 0 || f < best_f) { best = v; best_f = f; }
+        }
+        if (best < 0)
+            for (int v : trav)
+                if (!done[v]) { best = v; break; }
+        out.push_back(best);
+        done[best] = 1;
+    }
+    *order = out;
+}
+
 gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t flags,
                     gs_plan** out) {
     *out = nullptr;
@@ -274,6 +333,8 @@ gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t 
         }
     }
     for (int v = 0; v < k; ++v) materialize(v);   // not reached by any group (cannot happen)
+    if (g && !g->lab_rows[0].empty() && order.size() > 2) greedy_levels(g, pat, n, &order);
+    for (size_t l = 0; l < order.size(); ++l) level_of[order[l]] = (int)l;
     P->n_levels = (int)order.size();
     bool need_scan = false, too_many_probes = false;
     for (int l = 0; l < P->n_levels; ++l) {

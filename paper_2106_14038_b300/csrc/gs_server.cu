@@ -84,6 +84,7 @@ struct gs_server {
     uint64_t next_id = 1;
     uint64_t inflight_bytes = 0, peak_bytes = 0;
     uint64_t completed = 0, batches = 0, passed = 0;
+    uint64_t launches = 0, scans = 0, scan_plans = 0;   // of the completed batches
     gs_status fatal = GS_OK;
 };
 
@@ -119,6 +120,9 @@ void admit_add(Admit& a, const Ticket& t) {
 void complete(gs_server* s, std::shared_ptr<Flight>& f, gs_status rc) {
     std::vector<uint64_t> rows(f->tickets.size(), 0);
     if (rc == GS_OK) rc = gs_batch_info(f->b, rows.data(), nullptr);   // ready: no wait
+    uint32_t launches = 0, scans = 0, scan_plans = 0;
+    if (rc == GS_OK) gs_batch_stats(f->b, nullptr, &launches, nullptr);
+    if (rc == GS_OK) gs_batch_scans(f->b, &scans, &scan_plans);
     std::string msg = f->msg;
     if (rc != GS_OK && msg.empty()) msg = last_error();
     std::lock_guard<std::mutex> lk(s->mu);
@@ -134,6 +138,9 @@ void complete(gs_server* s, std::shared_ptr<Flight>& f, gs_status rc) {
     }
     s->stream_busy[f->stream] = 0;
     s->completed += f->tickets.size();
+    s->launches += launches;
+    s->scans += scans;
+    s->scan_plans += scan_plans;
 }
 
 void worker_loop(gs_server* s) {
@@ -426,6 +433,15 @@ gs_status gs_server_admission(gs_server* s, uint64_t* passed, uint64_t* inflight
     return GS_OK;
 }
 
+gs_status gs_server_work(gs_server* s, uint64_t* launches, uint64_t* scans, uint64_t* scan_plans) {
+    if (!s) { set_error("gs_server_work: NULL argument"); return GS_EINVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (launches) *launches = s->launches;
+    if (scans) *scans = s->scans;
+    if (scan_plans) *scan_plans = s->scan_plans;
+    return GS_OK;
+}
+
 gs_status gs_server_stats(gs_server* s, uint64_t* completed, uint64_t* batches,
                           uint64_t* peak_bytes) {
     if (!s) { set_error("gs_server_stats: NULL argument"); return GS_EINVAL; }
@@ -458,7 +474,9 @@ void gs_server_stop(gs_server* s) {
 
 extern "C" gs_status gs_server_replay(gs_server* s, const gs_plan* const* plans, uint32_t n_plans,
                                       const double* arrival_s, uint64_t n, double timeout_s,
-                                      double* latency_us, double* done_s) {
+                                      double* latency_us, double* done_s, int32_t* fetch_buf,
+                                      uint64_t fetch_cap_rows, uint64_t* fetched_bytes) {
+    if (fetched_bytes) *fetched_bytes = 0;
     if (!s || (n && (!plans || !arrival_s || n_plans == 0))) {
         set_error("gs_server_replay: NULL argument");
         return GS_EINVAL;
@@ -488,6 +506,14 @@ extern "C" gs_status gs_server_replay(gs_server* s, const gs_plan* const* plans,
                 else { state = it->second.state; done_at = it->second.done_at; if (state == 3) fail = it->second.err; }
             }
             if (state < 2) break;
+            if (fetch_buf && state == 2) {   // the answers to host memory before release
+                uint64_t rows = 0;
+                int d = 0;
+                gs_server_poll(s, ticket[head], &d, &rows, nullptr);
+                const gs_status rc = gs_server_fetch(s, ticket[head], fetch_buf, fetch_cap_rows, 0, 0);
+                if (rc != GS_OK) return rc;
+                if (fetched_bytes) *fetched_bytes += 4ull * rows * (uint64_t)plans[head % n_plans]->n_vars;
+            }
             if (latency_us) latency_us[head] = std::chrono::duration<double, std::micro>(done_at - t0).count() - arrival_s[head] * 1e6;
             if (done_s) done_s[head] = since(done_at);
             gs_server_release(s, ticket[head]);

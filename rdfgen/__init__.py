@@ -407,7 +407,7 @@ def rare_cycle(k: int, pendant: bool = False) -> Shape:
 
 def _shapes_bandwidth(w: Workload, n: int):
     """Constant-free cycles, in turn: 3-cycle, 4-cycle, 3-cycle with a
-    pendant edge on the root, 4-cycle with one. The root (vertex 0, where
+    pendant edge on the root, 4-cycle. The root (vertex 0, where
     the degree-driven traversal starts) is evaluated first with all its
     edges together (Sec. 5): its closing edge takes one of the 8 most
     frequent predicates, so expanding it from the root's candidates reads
@@ -418,7 +418,7 @@ def _shapes_bandwidth(w: Workload, n: int):
     out = []
     for q in range(n):
         kind = q % 4
-        sh = rare_cycle(3 if kind in (0, 2) else 4, pendant=kind >= 2)
+        sh = rare_cycle(3 if kind in (0, 2) else 4, pendant=kind == 2)
         for e in range(len(sh.edges)):
             sh.pred_range[e] = top if e == len(sh.edges) - 1 else tail
         assert bandwidth_root(sh) == 0
@@ -481,6 +481,20 @@ def load_queries(path: str):
             k = int(-pat[:, [0, 2]][pat[:, [0, 2]] < 0].min())
             out.append(Query(pat, k, t[0], float(t[1]), np.zeros(0, np.uint32)))
     return out
+
+
+BANDWIDTH_FILE = os.path.join(_HERE, "rmat26_bandwidth.txt")
+
+
+def bandwidth_workload(w: Workload | None = None):
+    """The bandwidth-bound workload's queries as written by
+    make_bandwidth_queries.py (the same selection as bandwidth_queries on
+    the scale-26 graph, stored so that a run needs no sampler)."""
+    w = w or WORKLOADS["rmat26"]
+    qs = load_queries(BANDWIDTH_FILE)
+    if len(qs) != w.n_queries:
+        raise ValueError("%s holds %d queries, the workload %d" % (BANDWIDTH_FILE, len(qs), w.n_queries))
+    return qs
 
 
 def queries(w: Workload, sampler: Sampler, n: int | None = None):

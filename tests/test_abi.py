@@ -120,7 +120,7 @@ def test_null_arguments_are_a_status_not_a_crash():
     assert lib.gs_eval_batch_cfg(None, None, 1, ctypes.byref(cfg), None, ctypes.byref(h)) == 1
     assert lib.gs_batch_autotune(None, None, 1, None, ctypes.byref(cfg), ctypes.byref(ms)) == 1
     assert lib.gs_server_start(None, None, ctypes.byref(h)) == 1
-    assert lib.gs_server_replay(None, None, 0, None, 0, 1.0, None, None) == 1
+    assert lib.gs_server_replay(None, None, 0, None, 0, 1.0, None, None, None, 0, None) == 1
     assert lib.gs_scan_candidates(None, None, None, 0, None, None) == 1
     assert lib.gs_scan_candidates_noalloc(None, None, None, 0, None, None) == 1
     assert lib.gs_batch_info(None, None, None) == 1

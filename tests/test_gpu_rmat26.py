@@ -1,0 +1,70 @@
+"""The bandwidth-bound workload end to end at full size: the constant-free
+cycles of rdfgen/rmat26_bandwidth.txt on the scale-26 graph (1.07e9
+triples), each starting with a triple scan over every label, evaluated one
+at a time, as one batch (shared scans) and through the server, row for row
+against the oracle. The oracle's index needs about 40 GB of host memory
+beside the 13 GB of triples; without it the test is skipped, saying so."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2106_14038_b300 as gs
+import rdfgen
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _host_gb():
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 2**20
+    return 0.0
+
+
+@pytest.fixture(scope="module")
+def rmat26():
+    need = 60.0
+    if _host_gb() < need:
+        pytest.skip("host memory: %.0f GB available, the scale-26 oracle needs about %.0f GB"
+                    % (_host_gb(), need))
+    w = rdfgen.WORKLOADS["rmat26"]
+    s, p, o = rdfgen.graph(w)
+    g = gs.Graph(s, p, o, w.n_vertices, w.n_preds)
+    ix = oracle.Index(s, p, o, w.n_vertices, w.n_preds)
+    del s, p, o
+    qs = rdfgen.bandwidth_workload(w)
+    threads = os.cpu_count() or 1
+    want = [ix.eval(q.patterns, threads=threads) for q in qs]
+    yield w, g, qs, want
+    g.close()
+
+
+def test_bandwidth_workload_one_at_a_time(rmat26):
+    w, g, qs, want = rmat26
+    for q, wnt in zip(qs, want):
+        assert q.bound >= len(wnt) >= 1 and len(wnt) <= w.cap
+        assert np.array_equal(g.query(q.patterns), wnt), q.shape
+
+
+def test_bandwidth_workload_batched_and_served(rmat26):
+    w, g, qs, want = rmat26
+    plans = [g.plan(q.patterns) for q in qs]
+    for frontier in (1, 2):
+        b = g.eval_batch(plans, config=gs.BatchConfig(frontier=frontier))
+        for i in range(len(qs)):
+            assert np.array_equal(b.fetch(i), want[i]), (frontier, qs[i].shape)
+        n_scans, n_plans = b.scans()
+        assert n_plans == len(qs) and n_scans < len(qs)
+        b.close()
+    srv = gs.Server(g)
+    try:
+        tickets = srv.submit_many(plans)
+        for t, wnt in zip(tickets, want):
+            while not srv.poll(t)[0]:
+                pass
+            assert np.array_equal(srv.fetch(t), wnt)
+    finally:
+        srv.stop()
