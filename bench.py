@@ -725,7 +725,12 @@ def run_query(args):
             if rep >= args.warmup:
                 dev[i].append(ms)
                 launches += nl
-            info[i] = (qs[i].shape, n, nl)
+            if rep == 0:
+                try:
+                    tree = r.tree()
+                except gs.GsError:
+                    tree = None
+                info[i] = (qs[i].shape, n, nl, tree, g.estimate(plan))
             r.close()
             plan.close()
     print(json.dumps({
@@ -733,7 +738,9 @@ def run_query(args):
         "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
         "config": {"workload": w.name, "queries": sel},
         "queries": [{"index": i, "shape": info[i][0], "rows": info[i][1], "launches": info[i][2],
-                     "device_ms": float(np.mean(dev[i]))} for i in sel],
+                     "tree_nodes": info[i][3], "estimate_bytes": info[i][4][0],
+                     "estimate_rows": info[i][4][1], "device_ms": float(np.mean(dev[i]))}
+                    for i in sel],
         "gpu_launches": launches,
     }), flush=True)
 

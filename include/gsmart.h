@@ -184,6 +184,12 @@ gs_status gs_result_info(gs_result* r, uint64_t* n_rows, uint32_t* n_vars);
 gs_status gs_fetch_bindings(gs_result* r, int32_t* dst, uint64_t cap_rows, int dst_on_device,
                             int sort_rows);
 
+/* The binding tree of r's last grid-path evaluation (Sec. 7.1): nodes per
+ * level into nodes[0 .. *n_levels) (waits like gs_result_info).
+ * GS_EOVERFLOW when cap < the plan's levels; GS_ENOTIMPL when the query
+ * ran in the single-CTA kernel (its levels are not kept). */
+gs_status gs_result_tree(gs_result* r, uint64_t* nodes, uint32_t cap, uint32_t* n_levels);
+
 /* Statistics of the last evaluation of r (synchronizes): device time in
  * milliseconds from CUDA events around the enqueued work, and the number of
  * kernels it launched. For a query the single CTA handed back, both cover
@@ -248,8 +254,8 @@ gs_status gs_eval_batch_cfg(gs_graph* g, const gs_plan* const* plans, uint32_t n
  * with the smallest wall time from enqueue to the last answer count, which
  * goes to *best_ms (may be NULL). Stage 1 tries CTAs per SM x candidate
  * budget x row budget; stage 2, when the sample holds plans with a triple
- * scan, tries shared or per-plan scans x bitmap or list frontier under the
- * stage-1 choice. The choice is kept for the life of the process, keyed by
+ * scan, tries shared or per-plan scans x bitmap or list frontier x 4 or 16
+ * grid-path streams under the stage-1 choice. The choice is kept for the life of the process, keyed by
  * the device name, the graph's N, M and P and the sample's shape classes
  * (scan or seeded, levels, leaves); a later call with the same key returns
  * it without timing. Synchronizes cuda_stream; answers are discarded.

@@ -37,7 +37,8 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_batch_autotune", "gs_server_replay", "gs_scan_status", "gs_batch_scans",
             "gs_plan_estimate", "gs_server_ticket", "gs_server_admission",
             "gs_server_submit_many", "gs_lspm_build", "gs_lspm_for_plan", "gs_lspm_info",
-            "gs_lspm_export", "gs_eval_query_lspm", "gs_free_lspm", "gs_server_work"]
+            "gs_lspm_export", "gs_eval_query_lspm", "gs_free_lspm", "gs_server_work",
+            "gs_result_tree"]
 
 
 class GsError(RuntimeError):
@@ -135,6 +136,7 @@ def load_library(path: str | None = None):
         "gs_result_info": [vp, P(u64), P(u32)],
         "gs_fetch_bindings": [vp, vp, u64, i32, i32],
         "gs_result_stats": [vp, P(ctypes.c_float), P(u32)],
+        "gs_result_tree": [vp, vp, u32, P(u32)],
         "gs_scan_candidates": [vp, vp, vp, u32, vp, vp],
         "gs_scan_candidates_noalloc": [vp, vp, vp, u32, vp, vp],
         "gs_scan_status": [vp, vp],
@@ -658,6 +660,13 @@ class Result:
         n = ctypes.c_uint32()
         _check(_lib.gs_result_stats(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return float(ms.value), int(n.value)
+
+    def tree(self):
+        """Nodes per level of the binding tree (grid-path evaluations)."""
+        buf = np.zeros(32, np.uint64)
+        n = ctypes.c_uint32()
+        _check(_lib.gs_result_tree(self._h, buf.ctypes.data_as(ctypes.c_void_p), 32, ctypes.byref(n)))
+        return buf[:n.value].tolist()
 
     def time_ms(self) -> float:
         return self.stats()[0]

@@ -664,6 +664,23 @@ gs_status gs_result_info(gs_result* r, uint64_t* n_rows, uint32_t* n_vars) {
     return GS_OK;
 }
 
+gs_status gs_result_tree(gs_result* r, uint64_t* nodes, uint32_t cap, uint32_t* n_levels) {
+    if (!r || !n_levels) { set_error("gs_result_tree: NULL argument"); return GS_EINVAL; }
+    gs_status rc = wait_result(r);
+    if (rc != GS_OK) return rc;
+    const int nl = r->plan.n_levels;
+    *n_levels = (uint32_t)nl;
+    if (r->mode == 1) {   // the single-CTA kernel kept its levels in its own workspace
+        set_error("gs_result_tree: the query ran in one CTA; its level sizes are not kept");
+        return GS_ENOTIMPL;
+    }
+    if (!nodes || cap < (uint32_t)nl) { set_error("gs_result_tree: room for %u levels, need %d", cap, nl); return GS_EOVERFLOW; }
+    Ctl head;
+    std::memcpy(&head, r->head, kCtlHead);
+    for (int l = 0; l < nl; ++l) nodes[l] = head.n[l];
+    return GS_OK;
+}
+
 gs_status gs_result_stats(gs_result* r, float* device_ms, uint32_t* kernel_launches) {
     if (!r) { set_error("gs_result_stats: result is NULL"); return GS_EINVAL; }
     gs_status rc = wait_result(r);

@@ -293,6 +293,8 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
     b->st = (cudaStream_t)cuda_stream;
     b->n = n;
     b->cfg = resolve(g, cfg);
+    // batches that run at once (a server's) spread over the side streams
+    b->next_side = g->side_rr.fetch_add(b->cfg.grid_streams);
     b->plans.assign(plans, plans + n);
     b->n_vars.resize(n);
     b->in_kernel.assign(n, 0);
@@ -700,19 +702,22 @@ extern "C" gs_status gs_batch_autotune(gs_graph* g, const gs_plan* const* plans,
                 if (consider(cfg) != GS_OK) return rc;
             }
     // stage 2, for samples with triple scans: shared or per-plan scans x
-    // bitmap or list frontier, under the stage-1 choice
+    // bitmap or list frontier x grid-path queries side by side, under the
+    // stage-1 choice
     if (scans) {
         const gs_batch_config base = *best;
         for (uint32_t share : {1u, 2u})
-            for (uint32_t fr : {1u, 2u}) {
-                if (fr == 2 && !lists) continue;
-                cfg = base;
-                cfg.scan_share = share;
-                cfg.frontier = fr;
-                if (consider(cfg) != GS_OK) return rc;
-            }
+            for (uint32_t fr : {1u, 2u})
+                for (uint32_t gsn : {kGridStreams, 16u}) {
+                    if (fr == 2 && !lists) continue;
+                    cfg = base;
+                    cfg.scan_share = share;
+                    cfg.frontier = fr;
+                    cfg.grid_streams = gsn;
+                    if (consider(cfg) != GS_OK) return rc;
+                }
     }
-    best->grid_streams = kGridStreams;
+    if (best->grid_streams == 0) best->grid_streams = kGridStreams;
     if (best->scan_share == 0) best->scan_share = 1;
     if (best->frontier == 0) best->frontier = 1;
     if (best_ms) *best_ms = (float)best_t;

@@ -71,8 +71,12 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__
     return lo + below;
 }
 
+static_assert(kShort == kDirMin, "rows without a label directory are the short ones");
+
 // Entries of predicate p in row r: [lo, lo + len) of S.idx. Rows are sorted
-// by (label, idx), so this is Eq. 8's S_p (x) A restricted to one row.
+// by (label, idx), so this is Eq. 8's S_p (x) A restricted to one row. A
+// long row is looked up in its label directory (one entry per run of equal
+// labels, at most P) instead of its whole label array.
 __device__ __forceinline__ void label_range(const DStore& S, uint32_t r, uint32_t p, uint32_t& lo,
                                             uint32_t& len) {
     const uint32_t b = ld(S.ptr + r), e = ld(S.ptr + r + 1);
@@ -81,6 +85,18 @@ __device__ __forceinline__ void label_range(const DStore& S, uint32_t r, uint32_
         count_short(S.lab, b, e, p, below, equal);
         lo = b + below;
         len = equal;
+        return;
+    }
+    if (S.dir_off) {
+        const uint32_t d0 = ld(S.dir_off + r), d1 = ld(S.dir_off + r + 1);
+        const uint32_t j = lower_bound_u32(S.dir_lab, d0, d1, p);
+        if (j < d1 && ld(S.dir_lab + j) == p) {
+            lo = ld(S.dir_pos + j);
+            len = (j + 1 < d1 ? ld(S.dir_pos + j + 1) : e) - lo;
+        } else {
+            lo = b;
+            len = 0;
+        }
         return;
     }
     const uint32_t l = lower_bound_u32(S.lab, b, e, p);
@@ -96,6 +112,11 @@ __device__ __forceinline__ bool has_label(const DStore& S, uint32_t r, uint32_t 
         uint32_t below, equal;
         count_short(S.lab, b, e, p, below, equal);
         return equal != 0;
+    }
+    if (S.dir_off) {
+        const uint32_t d0 = ld(S.dir_off + r), d1 = ld(S.dir_off + r + 1);
+        const uint32_t j = lower_bound_u32(S.dir_lab, d0, d1, p);
+        return j < d1 && ld(S.dir_lab + j) == p;
     }
     const uint32_t l = lower_bound_u32(S.lab, b, e, p);
     return l < e && ld(S.lab + l) == p;

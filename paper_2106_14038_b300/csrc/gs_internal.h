@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cstdint>
 #include <mutex>
@@ -92,16 +93,30 @@ struct Store {
     // bit k of heads: entry k is the first entry of its row
     // (M / 32 + 8 words, zero past the last entry)
     uint32_t* heads = nullptr;
+    // label directory of the rows longer than kDirMin entries: the runs of
+    // equal labels of row r are dir_lab / dir_pos [dir_off[r], dir_off[r+1])
+    // (label, first entry); shorter rows have none. NULL when not built.
+    uint32_t* dir_off = nullptr;
+    uint32_t* dir_lab = nullptr;
+    uint32_t* dir_pos = nullptr;
+    uint64_t dir_runs = 0;
 };
+
+constexpr uint32_t kDirMin = 32;   // rows up to this long are searched directly
 
 // Device view passed to kernels by value.
 struct DStore {
     const uint32_t* __restrict__ ptr;
     const uint32_t* __restrict__ idx;
     const uint32_t* __restrict__ lab;
+    const uint32_t* __restrict__ dir_off;   // NULL: no label directory
+    const uint32_t* __restrict__ dir_lab;
+    const uint32_t* __restrict__ dir_pos;
 };
 
-inline DStore dview(const Store& s) { return DStore{s.ptr, s.idx, s.lab}; }
+inline DStore dview(const Store& s) {
+    return DStore{s.ptr, s.idx, s.lab, s.dir_off, s.dir_lab, s.dir_pos};
+}
 
 }  // namespace gs
 
@@ -118,6 +133,7 @@ struct gs_graph {
     // side by side (created on first use, destroyed with the graph)
     cudaStream_t side[16] = {};
     int n_side = 0;
+    std::atomic<uint32_t> side_rr{0};   // where the next batch starts on the side streams
     // host copies of the row lengths (out = CSR, in = CSC), used to route
     // queries whose first level is certainly large away from the
     // single-CTA evaluator

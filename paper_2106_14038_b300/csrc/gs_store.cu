@@ -14,6 +14,8 @@
 
 namespace gs {
 
+__global__ void k_u64_to_u32(const uint64_t* __restrict__ a, uint64_t n, uint32_t* __restrict__ b);
+
 constexpr int kRsWarps = kThreads / 32;
 constexpr int kRsRounds = 16;
 constexpr int kRsTile = kRsWarps * 32 * kRsRounds;   // 4096 keys per block tile
@@ -313,6 +315,67 @@ gs_status store_items(const gs_graph* g, Store& S, uint64_t M, cudaStream_t st) 
     return GS_OK;
 }
 
+// Label directory (see Store): a row longer than kDirMin is walked run by
+// run, each step jumping past the current label with a search (at most P
+// runs per row), to count its runs (write = 0) or write them.
+__global__ void k_dir_rows(const uint32_t* __restrict__ ptr, const uint32_t* __restrict__ lab,
+                           uint32_t N, uint64_t* __restrict__ cnt, const uint64_t* __restrict__ off,
+                           uint32_t* __restrict__ dlab, uint32_t* __restrict__ dpos, int write) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = ptr[r], e = ptr[r + 1];
+        uint64_t c = 0;
+        if (e - b > kDirMin) {
+            uint64_t at = write ? off[r] : 0;
+            for (uint32_t j = b; j < e;) {
+                const uint32_t l = lab[j];
+                if (write) { dlab[at] = l; dpos[at] = j; ++at; }
+                ++c;
+                j = lower_bound_u32(lab, j, e, l + 1);
+            }
+        }
+        if (!write) cnt[r] = c;
+    }
+}
+
+// Builds S's label directory (dir_off over the N rows, u32: the runs are at
+// most M < 2^32). Synchronizes st.
+static gs_status build_label_dir(const gs_graph* g, Store& S, cudaStream_t st) {
+    const uint32_t N = g->N;
+    const int nb = g->n_blocks;
+    uint64_t* cnt = (uint64_t*)g->alloc.get(sizeof(uint64_t) * ((uint64_t)N + 1), st);
+    uint64_t* misc = (uint64_t*)g->alloc.get(sizeof(uint64_t) * (2 * kBlocks + 8), st);
+    auto done = [&](gs_status r) { g->alloc.put(cnt, st); g->alloc.put(misc, st); return r; };
+    if (!cnt || !misc) { set_error("gs_load_triples: out of device memory (label directory)"); return done(GS_ENOMEM); }
+    uint64_t* bsum = misc;
+    uint64_t* boff = misc + kBlocks;
+    uint64_t* total = misc + 2 * kBlocks;
+    uint64_t* n_dev = total + 1;
+    const uint64_t n_host = (uint64_t)N + 1;
+    GS_CUDA(cudaMemcpyAsync(n_dev, &n_host, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemsetAsync(cnt + N, 0, sizeof(uint64_t), st));
+    k_dir_rows<<<nb, kThreads, 0, st>>>(S.ptr, S.lab, N, cnt, nullptr, nullptr, nullptr, 0);
+    k_block_sums_u64<<<nb, kThreads, 0, st>>>(cnt, n_dev, bsum, nullptr);
+    k_scan_block_sums<<<1, kThreads, 0, st>>>(bsum, boff, (uint32_t)nb, total, nullptr);
+    k_scan_apply_u64<<<nb, kThreads, 0, st>>>(cnt, n_dev, boff, nullptr);   // cnt[r]: first run of row r
+    uint64_t runs = 0;
+    GS_CUDA(cudaMemcpyAsync(&runs, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    S.dir_runs = runs;
+    S.dir_off = (uint32_t*)g->alloc.get(sizeof(uint32_t) * ((uint64_t)N + 1 + 4), st);
+    S.dir_lab = (uint32_t*)g->alloc.get(sizeof(uint32_t) * (runs + 4), st);
+    S.dir_pos = (uint32_t*)g->alloc.get(sizeof(uint32_t) * (runs + 4), st);
+    if (!S.dir_off || !S.dir_lab || !S.dir_pos) { set_error("gs_load_triples: out of device memory (label directory)"); return done(GS_ENOMEM); }
+    GS_CUDA(cudaMemsetAsync(S.dir_lab + runs, 0, 16, st));   // padding read by 16-byte loads
+    GS_CUDA(cudaMemsetAsync(S.dir_pos + runs, 0, 16, st));
+    GS_CUDA(cudaMemsetAsync(S.dir_off + N + 1, 0, 16, st));
+    k_dir_rows<<<nb, kThreads, 0, st>>>(S.ptr, S.lab, N, nullptr, cnt, S.dir_lab, S.dir_pos, 1);
+    k_u64_to_u32<<<nb, kThreads, 0, st>>>(cnt, (uint64_t)N + 1, S.dir_off);
+    GS_CUDA(cudaGetLastError());
+    GS_CUDA(cudaStreamSynchronize(st));
+    return done(GS_OK);
+}
+
 // Per predicate label l of one orientation: cnt[l] = entries with label l,
 // rows[l] = rows holding label l. Rows are sorted by (label, other end), so
 // the entries of (row, l) form one run: a run starts at a row start or
@@ -363,6 +426,12 @@ static gs_status label_stats(gs_graph* g, cudaStream_t st) {
     return GS_OK;
 }
 
+__global__ void k_u64_to_u32(const uint64_t* __restrict__ a, uint64_t n, uint32_t* __restrict__ b) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        b[i] = (uint32_t)a[i];
+}
+
 gs_status build_store(gs_graph* g, const uint32_t* s, const uint32_t* p, const uint32_t* o,
                       uint64_t n, bool on_device, cudaStream_t st) {
     const int vb = bits_for(g->N ? g->N - 1 : 0);
@@ -391,6 +460,8 @@ gs_status build_store(gs_graph* g, const uint32_t* s, const uint32_t* p, const u
     if (!k0 || !k1 || !misc) { set_error("gs_load_triples: out of device memory for sort keys"); rc = GS_ENOMEM; }
     if (rc == GS_OK) rc = build_dir(g, ds, dp, dpo, n, 0, vb, lb, k0, k1, misc, g->out, st);
     if (rc == GS_OK) rc = build_dir(g, ds, dp, dpo, n, 1, vb, lb, k0, k1, misc, g->in, st);
+    if (rc == GS_OK) rc = build_label_dir(g, g->out, st);
+    if (rc == GS_OK) rc = build_label_dir(g, g->in, st);
     if (rc == GS_OK) rc = label_stats(g, st);
     g->alloc.put(k0, st);
     g->alloc.put(k1, st);
@@ -406,6 +477,9 @@ void free_store(gs_graph* g, cudaStream_t st) {
         g->alloc.put(S->ptr, st); g->alloc.put(S->idx, st); g->alloc.put(S->lab, st);
         g->alloc.put(S->items, st);
         g->alloc.put(S->heads, st);
+        g->alloc.put(S->dir_off, st);
+        g->alloc.put(S->dir_lab, st);
+        g->alloc.put(S->dir_pos, st);
         *S = Store{};
     }
 }
