@@ -46,7 +46,7 @@ def _args():
                     help="budget of the CPU oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mode", default="plain",
-                    choices=["plain", "scan", "batched", "served", "query"],
+                    choices=["plain", "scan", "batched", "served", "query", "paths"],
                     help="plain: the workload's queries one at a time (the headline line); "
                          "scan: the triple scan alone; batched: the batched workload "
                          "(rmat24: 4,096 queries in one launch) against one at a time; "
@@ -948,8 +948,47 @@ def _scan_roofline(g, w, stream, peaks, which, n_scan=20):
             "ms_median": float(np.median(ms))}
 
 
+def run_paths(args):
+    """Per-path binding trees (GS_PLAN_PATHS: one tree per path, tree-pruning,
+    join) against the path-linearized tree on the workload's stars,
+    snowflakes and cycles, both on the grid path: binding-tree nodes (the
+    memory the trees take), answer rows (equal) and device time."""
+    import torch
+    torch.cuda.set_device(0)
+    os.environ["GS_EXEC"] = "grid"          # tree sizes are kept on the grid path
+    import paper_2106_14038_b300 as gs
+    w, triples, qs = _workload(args.workload)
+    g = gs.Graph(*triples, w.n_vertices, w.n_preds)
+    stream = torch.cuda.current_stream()
+    out = []
+    for i, q in enumerate(qs):
+        if not q.shape.startswith(("star", "snowflake", "cycle")):
+            continue
+        row = {"index": i, "shape": q.shape}
+        for name, flags in (("linear", gs.PLAN_DEGREE), ("paths", gs.PLAN_PATHS)):
+            plan = g.plan(q.patterns, flags)
+            ms = []
+            for rep in range(args.warmup + args.steps):
+                r = g.eval(plan, stream)
+                n, _ = r.info()
+                if rep >= args.warmup:
+                    ms.append(r.stats()[0])
+                tree = r.tree()
+                r.close()
+            row[name] = {"rows": n, "tree_nodes": int(sum(tree)), "per_tree": tree,
+                         "device_ms": float(np.mean(ms))}
+            plan.close()
+        assert row["linear"]["rows"] == row["paths"]["rows"], row
+        out.append(row)
+    print(json.dumps({"metric": "binding-tree nodes and device ms, per-path vs linearized",
+                      "config": {"workload": w.name}, "queries": out}), flush=True)
+
+
 def main():
     args = _args()
+    if args.mode == "paths":
+        run_paths(args)
+        return
     if args.impl == "gsmart" and args.mode == "plain" and args.workload == "rmat26":
         run_bandwidth(args)
         return

@@ -119,6 +119,10 @@ gs_status gs_graph_export(const gs_graph* g, int by_column, uint32_t* ptr, uint3
  * Host only. */
 #define GS_PLAN_DEGREE 0u
 #define GS_PLAN_DIRECTION 1u
+#define GS_PLAN_PATHS 4u      /* option bit: evaluate with one binding tree per
+                                 path of the traversal (Sec. 7.1), reconciled
+                                 by local and global tree-pruning (Sec. 8.1,
+                                 8.2) and joined into the answers */
 #define GS_PLAN_LISTS 2u      /* option bit: for a plan with a triple scan, only
                                  the levels listed from the scan (roots) get a
                                  candidate vector; later levels check the
@@ -137,6 +141,15 @@ gs_status gs_plan_query(const gs_graph* g, const int64_t* patterns, uint32_t n_p
  * vertex id c. *len receives the word count; GS_EOVERFLOW (nothing
  * written) when cap is smaller. */
 gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint32_t* len);
+
+/* The binding-tree paths of the plan (Sec. 7.1, Ex. 7.1) as int32 words:
+ *   [n_paths, then per path: n_vertices, variable indices...]
+ * from each root, each edge of a group is followed to its other end, and
+ * into that end's group when this edge first reached it, else the path
+ * ends; self-loops and edges to constants do not extend a path, and a
+ * variable no path reaches is a path of its own. *len receives the word
+ * count; GS_EOVERFLOW (nothing written) when cap is smaller. */
+gs_status gs_plan_paths(const gs_plan* plan, int32_t* buf, uint32_t cap, uint32_t* len);
 
 /* ------------------------------------------------------------------ */
 /* Evaluation (Sec. 5, Sec. 7): grouped incident-edge evaluation of the

@@ -18,11 +18,12 @@ import numpy as np
 from ._build import LIB, build
 
 __all__ = ["Graph", "Plan", "Result", "Batch", "Server", "GsError", "TorchAllocator", "load_library", "PLAN_DEGREE",
-           "PLAN_DIRECTION", "PLAN_LISTS", "BatchConfig", "Lspm", "build"]
+           "PLAN_DIRECTION", "PLAN_LISTS", "PLAN_PATHS", "BatchConfig", "Lspm", "build"]
 
 PLAN_DEGREE = 0
 PLAN_DIRECTION = 1
 PLAN_LISTS = 2         # option bit: the list frontier form
+PLAN_PATHS = 4         # option bit: per-path binding trees with tree-pruning
 _STATUS = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOMEM", 3: "GS_ECUDA", 4: "GS_EOVERFLOW",
            5: "GS_ETIMEOUT", 6: "GS_ENOTIMPL"}
 
@@ -38,7 +39,7 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_plan_estimate", "gs_server_ticket", "gs_server_admission",
             "gs_server_submit_many", "gs_lspm_build", "gs_lspm_for_plan", "gs_lspm_info",
             "gs_lspm_export", "gs_eval_query_lspm", "gs_free_lspm", "gs_server_work",
-            "gs_result_tree"]
+            "gs_result_tree", "gs_plan_paths"]
 
 
 class GsError(RuntimeError):
@@ -132,6 +133,7 @@ def load_library(path: str | None = None):
         "gs_graph_export": [vp, i32, vp, vp, vp, i32, vp],
         "gs_plan_query": [vp, vp, u32, u32, P(vp)],
         "gs_plan_describe": [vp, vp, u32, P(u32)],
+        "gs_plan_paths": [vp, vp, u32, P(u32)],
         "gs_eval_query": [vp, vp, vp, P(vp)],
         "gs_result_info": [vp, P(u64), P(u32)],
         "gs_fetch_bindings": [vp, vp, u64, i32, i32],
@@ -465,6 +467,20 @@ class Plan:
         nr = w[i]; i += 1
         roots = [vert(x) for x in w[i:i + nr]]
         return groups, roots
+
+    def paths(self):
+        """Binding-tree paths (Sec. 7.1): lists of variable indices."""
+        n = ctypes.c_uint32()
+        _lib.gs_plan_paths(self._h, None, 0, ctypes.byref(n))
+        buf = np.zeros(max(1, n.value), np.int32)
+        _check(_lib.gs_plan_paths(self._h, buf.ctypes.data_as(ctypes.c_void_p), n.value,
+                                  ctypes.byref(n)))
+        w = buf[:n.value].tolist()
+        out, i = [], 1
+        for _ in range(w[0]):
+            out.append(w[i + 1:i + 1 + w[i]])
+            i += 1 + w[i]
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

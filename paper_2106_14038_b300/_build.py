@@ -11,7 +11,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsmart.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["gs_util.cu", "gs_store.cu", "gs_scan.cu", "gs_exec.cu", "gs_small.cu", "gs_batch.cu", "gs_server.cu", "gs_api.cu",
-           "gs_noalloc.cu", "gs_lspm.cu", "gs_plan.cpp"]
+           "gs_noalloc.cu", "gs_lspm.cu", "gs_paths.cu", "gs_plan.cpp"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-Wall", "-I", INCLUDE]

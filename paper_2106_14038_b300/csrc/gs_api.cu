@@ -83,6 +83,8 @@ struct gs_result {
     // the orientations evaluated against (a per-query LSpM; NULL: the graph's)
     const Store* so = nullptr;
     const Store* si = nullptr;
+    bool bits_borrowed = false;   // bits belong to the caller (per-path evaluation)
+    std::vector<uint64_t> path_nodes;   // per-path mode: binding-tree nodes of each path
     uint32_t launches = 0;
     uint64_t rows = 0;
     uint64_t out_off = 0;
@@ -238,7 +240,7 @@ void release(gs_result* r) {
     if (r->g) {
         cudaStreamSynchronize(r->st);
         r->g->alloc.put(r->arena, r->st);
-        r->g->alloc.put(r->bits, r->st);
+        if (!r->bits_borrowed) r->g->alloc.put(r->bits, r->st);
         r->g->alloc.put(r->work, r->st);
         r->g->alloc.put(r->lists, r->st);
     }
@@ -343,6 +345,20 @@ gs_status gs_plan_query(const gs_graph* g, const int64_t* patterns, uint32_t n_p
                         uint32_t flags, gs_plan** out) {
     if (!out) { set_error("gs_plan_query: out is NULL"); return GS_EINVAL; }
     return make_plan(g, patterns, n_patterns, flags, out);
+}
+
+gs_status gs_plan_paths(const gs_plan* plan, int32_t* buf, uint32_t cap, uint32_t* len) {
+    if (!plan || !len) { set_error("gs_plan_paths: NULL argument"); return GS_EINVAL; }
+    std::vector<int32_t> w;
+    w.push_back((int32_t)plan->paths.size());
+    for (auto& p : plan->paths) {
+        w.push_back((int32_t)p.size());
+        for (int v : p) w.push_back(v);
+    }
+    *len = (uint32_t)w.size();
+    if (!buf || cap < w.size()) { set_error("gs_plan_paths: buffer holds %u words, need %zu", cap, w.size()); return GS_EOVERFLOW; }
+    std::memcpy(buf, w.data(), sizeof(int32_t) * w.size());
+    return GS_OK;
 }
 
 gs_status gs_plan_describe(const gs_plan* plan, int32_t* buf, uint32_t cap, uint32_t* len) {
@@ -485,7 +501,7 @@ gs_status gs::result_compact(gs_result* r) {
         GS_CUDA(cudaMemcpyAsync(keep, r->arena + r->out_off, 4ull * r->rows * r->plan.n_vars,
                                 cudaMemcpyDeviceToDevice, r->st));
     r->g->alloc.put(r->arena, r->st);
-    r->g->alloc.put(r->bits, r->st);
+    if (!r->bits_borrowed) r->g->alloc.put(r->bits, r->st);
     r->g->alloc.put(r->work, r->st);
     r->g->alloc.put(r->lists, r->st);
     r->bits = nullptr;
@@ -519,10 +535,52 @@ gs_status gs::eval_query_path(gs_graph* g, const gs_plan* plan, void* cuda_strea
     return eval_query_impl(g, plan, cuda_stream, force_grid, nullptr, nullptr, nullptr, out);
 }
 
+gs_status gs::eval_query_borrowed(gs_graph* g, const gs_plan* plan, void* cuda_stream,
+                                  uint32_t* bits, cudaEvent_t ready, const uint32_t* scan_status,
+                                  gs_result** out) {
+    gs_status rc = eval_query_impl(g, plan, cuda_stream, 1, bits, ready, scan_status, out);
+    if (rc == GS_OK) (*out)->bits_borrowed = true;
+    return rc;
+}
+
+gs_result* gs::result_new_table(gs_graph* g, const gs_plan* plan, cudaStream_t st) {
+    gs_result* r = new (std::nothrow) gs_result();
+    if (!r) return nullptr;
+    r->g = g;
+    r->plan = *plan;
+    r->st = st;
+    cudaEvent_t* ev[3] = {&r->ev0, &r->ev1, &r->ev2};
+    if (take_host_res(g, ev, &r->head) != GS_OK || cudaEventRecord(r->ev0, st) != cudaSuccess) {
+        release(r);
+        return nullptr;
+    }
+    return r;
+}
+
+gs_status gs::result_set_table(gs_result* r, int32_t* rows, uint64_t bytes, uint64_t n,
+                               uint32_t launches, const std::vector<uint64_t>& path_nodes) {
+    r->arena = (uint8_t*)rows;
+    r->arena_bytes = bytes;
+    r->out_off = 0;
+    r->rows = n;
+    r->launches = launches;
+    r->path_nodes = path_nodes;
+    GS_CUDA(cudaEventRecord(r->ev1, r->st));
+    GS_CUDA(cudaEventRecord(r->ev2, r->st));
+    r->ready = true;
+    return GS_OK;
+}
+
+void gs::result_free(gs_result* r) { release(r); }
+
+const int32_t* gs::result_rows(gs_result* r) {
+    return wait_result(r) == GS_OK ? (const int32_t*)(r->arena + r->out_off) : nullptr;
+}
+
 gs_status gs::eval_query_prescanned(gs_graph* g, const gs_plan* plan, void* cuda_stream,
                                     uint32_t* bits, cudaEvent_t ready, const uint32_t* scan_status,
                                     gs_result** out) {
-    if (!bits || !ready || !scan_status || !plan || !plan->needs_scan) {
+    if (!bits || !ready || !scan_status || !plan) {
         set_error("internal: a prescanned query needs its vectors, event and status word");
         return GS_EINVAL;
     }
@@ -608,6 +666,7 @@ gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, i
 extern "C" {
 
 gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out) {
+    if (plan && (plan->flags & GS_PLAN_PATHS)) return eval_paths(g, plan, cuda_stream, out);
     const char* how = getenv("GS_EXEC");   // "grid" forces the grid path
     return eval_query_path(g, plan, cuda_stream, how && !strcmp(how, "grid"), out);
 }
@@ -668,6 +727,12 @@ gs_status gs_result_tree(gs_result* r, uint64_t* nodes, uint32_t cap, uint32_t* 
     if (!r || !n_levels) { set_error("gs_result_tree: NULL argument"); return GS_EINVAL; }
     gs_status rc = wait_result(r);
     if (rc != GS_OK) return rc;
+    if (!r->path_nodes.empty()) {   // per-path mode: the tree of each path
+        *n_levels = (uint32_t)r->path_nodes.size();
+        if (!nodes || cap < *n_levels) { set_error("gs_result_tree: room for %u paths, need %u", cap, *n_levels); return GS_EOVERFLOW; }
+        for (uint32_t i = 0; i < *n_levels; ++i) nodes[i] = r->path_nodes[i];
+        return GS_OK;
+    }
     const int nl = r->plan.n_levels;
     *n_levels = (uint32_t)nl;
     if (r->mode == 1) {   // the single-CTA kernel kept its levels in its own workspace

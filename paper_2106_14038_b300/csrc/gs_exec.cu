@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
 __global__ void __launch_bounds__(kThreads) k_bits_count(ExecDev E, int l, LevelSpec L) {
     chain_enter();
     if (overflowed(E.ctl)) return;
-    const uint32_t* bm = E.bits + (uint64_t)l * E.words;
+    const uint32_t* bm = E.bits + (uint64_t)L.vec * E.words;
     uint64_t beg, end;
     block_chunk(E.words, blockIdx.x, gridDim.x, beg, end);
     uint64_t c = 0;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_bits_write(ExecDev E, int l, Level
     chain_enter();
     Ctl* ctl = E.ctl;
     if (overflowed(ctl) || ctl->dead) return;
-    const uint32_t* bm = E.bits + (uint64_t)l * E.words;
+    const uint32_t* bm = E.bits + (uint64_t)L.vec * E.words;
     uint64_t base_l = kCtlBytes;
     for (int j = 0; j < l; ++j) base_l += align256(8ull * ctl->n[j]);
     const uint64_t cap = E.arena_bytes > base_l ? (E.arena_bytes - base_l) / 8 : 0;

@@ -154,6 +154,21 @@ gs_status enqueue_small(const gs_plan* P, const ExecDev& E, uint32_t* launches, 
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
                        cudaStream_t st, int start_level = 0, const uint32_t* scanned = nullptr,
                        const Store* so = nullptr, const Store* si = nullptr);
+// As eval_query_prescanned, but bits stay the caller's (several results
+// read one set of candidate vectors).
+gs_status eval_query_borrowed(gs_graph* g, const gs_plan* plan, void* cuda_stream, uint32_t* bits,
+                              cudaEvent_t ready, const uint32_t* scan_status, gs_result** out);
+// A result whose answers are a table built outside the executor: created
+// (its start event recorded on st), then given the rows (device memory the
+// result takes over, n rows of the plan's variables in order).
+gs_result* result_new_table(gs_graph* g, const gs_plan* plan, cudaStream_t st);
+gs_status result_set_table(gs_result* r, int32_t* rows, uint64_t bytes, uint64_t n,
+                           uint32_t launches, const std::vector<uint64_t>& path_nodes);
+void result_free(gs_result* r);
+// The device rows of a finished result (waits for it; NULL on failure).
+const int32_t* result_rows(gs_result* r);
+// Per-path evaluation (gs_paths.cu) of a plan made with GS_PLAN_PATHS.
+gs_status eval_paths(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out);
 // Per-query LSpM (gs_lspm.cu): the (predicate, orientation) pairs a plan's
 // evaluation reads; an LSpM's orientation; whether an LSpM holds every pair
 // a plan reads.

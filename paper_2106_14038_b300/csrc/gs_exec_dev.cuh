@@ -71,7 +71,7 @@ __device__ __forceinline__ const DStore& store_of(const ExecDev& E, uint32_t dir
 __device__ __forceinline__ bool keep_candidate(const ExecDev& E, const LevelSpec& L, int l,
                                                uint32_t x, const uint2* rng, uint32_t sel) {
     if (L.use_bitmap) {
-        const uint32_t* bm = E.bits + (uint64_t)l * E.words;
+        const uint32_t* bm = E.bits + (uint64_t)L.vec * E.words;
         if (!((__ldg(bm + (x >> 5)) >> (x & 31)) & 1u)) return false;
     }
     for (int b = 0; b < L.n_binders; ++b) {

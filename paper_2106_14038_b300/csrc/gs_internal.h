@@ -186,6 +186,8 @@ struct LevelSpec {
     int32_t n_probes;
     int32_t n_self;
     int32_t use_bitmap;    // test candidates against the variable's candidate vector
+    int32_t vec;           // that vector: bits + vec * words (the level's own index
+                           // in an ordinary plan)
     Binder b[kMaxBinders];
     Probe pr[kMaxProbes];
     uint32_t self_label[kMaxSelf];
@@ -240,6 +242,12 @@ struct gs_plan {
     // (no level has more probes than kMaxProbes).
     bool list_ok = false;
     bool list_form = false;                // levels / scan hold the list form
+    // binding-tree paths of Sec. 7.1: variables from a root; step j > 0 is
+    // reached from step j - 1 through pattern path_pat[.][j] (-1 at j = 0).
+    // A variable no path reaches (its edges all go to constants) is a path
+    // of its own.
+    std::vector<std::vector<int>> paths, path_pat;
+    gs::ScanSpec path_scan{};   // with GS_PLAN_PATHS: one candidate vector per variable
     gs::LevelSpec levels_alt[gs::kMaxLevels];   // the other form's levels
     gs::ScanSpec scan_alt{};                    // the other form's scan
 };

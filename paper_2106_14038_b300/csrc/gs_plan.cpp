@@ -25,6 +25,7 @@
 // a single pattern to another variable is not materialized (a leaf).
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <set>
 
 #include "gs_internal.h"
@@ -188,6 +189,72 @@ void direction_driven(const QGraph& G, Groups& groups, std::vector<int>& roots) 
 
 }  // namespace
 
+// Binding-tree paths of Sec. 7.1 (Ex. 7.1): from each root, follow each
+// edge of its group to the other end; continue into that end's group when
+// this edge is the one that first reached it, else the path ends there.
+// Self-loops are checks at their variable's level and edges to constants
+// are its binders, so neither is a path step: a path also ends at a
+// variable whose group holds nothing else. A variable's group that no walk
+// enters (a constant's edge reached it first) starts paths of its own.
+static void make_paths(const QGraph& G, const Groups& groups, const std::vector<int>& roots, gs_plan* P) {
+    std::vector<int> group_of(G.V.size(), -1);
+    for (size_t i = 0; i < groups.size(); ++i) group_of[groups[i].first] = (int)i;
+    std::vector<int> reached_by(G.V.size(), -1);
+    std::vector<char> is_root(G.V.size(), 0);
+    for (int r : roots) is_root[r] = 1;
+    for (auto& gr : groups)
+        for (int e : gr.second) {
+            const int a = G.E[e].first, b = G.E[e].second;
+            const int w = a == gr.first ? b : a;
+            if (w == gr.first || G.V[w].is_const || is_root[w] || reached_by[w] >= 0) continue;
+            reached_by[w] = e;
+        }
+    std::vector<int> vars, pats;
+    std::vector<char> entered(G.V.size(), 0);
+    // returns whether a path was recorded below v
+    std::function<bool(int)> walk = [&](int v) {
+        bool any = false;
+        if (group_of[v] < 0) return any;
+        entered[v] = 1;
+        for (int e : groups[group_of[v]].second) {
+            const int a = G.E[e].first, b = G.E[e].second;
+            const int w = a == v ? b : a;
+            if (w == v || G.V[w].is_const) continue;
+            vars.push_back((int)G.V[w].id);
+            pats.push_back(e);
+            // into w's group when this edge first reached w; the path ends
+            // at w when nothing follows there (only self-loops or constants)
+            if (!(group_of[w] >= 0 && reached_by[w] == e && walk(w))) {
+                P->paths.push_back(vars);
+                P->path_pat.push_back(pats);
+            }
+            any = true;
+            vars.pop_back();
+            pats.pop_back();
+        }
+        return any;
+    };
+    for (int r : roots) {
+        if (G.V[r].is_const) continue;
+        vars.assign(1, (int)G.V[r].id);
+        pats.assign(1, -1);
+        walk(r);
+    }
+    // the group of a variable that a constant's edge reached first is
+    // entered by no walk: its paths start at that variable
+    for (auto& gr : groups) {
+        if (G.V[gr.first].is_const || entered[gr.first]) continue;
+        vars.assign(1, (int)G.V[gr.first].id);
+        pats.assign(1, -1);
+        walk(gr.first);
+    }
+    std::vector<char> covered(P->n_vars, 0);
+    for (auto& pth : P->paths)
+        for (int v : pth) covered[v] = 1;
+    for (int v = 0; v < P->n_vars; ++v)
+        if (!covered[v]) { P->paths.push_back({v}); P->path_pat.push_back({-1}); }
+}
+
 // Level order by estimated candidates. The first level stays the
 // traversal's (the root, or the variable its first constant binds); then,
 // repeatedly, the variable whose cheapest edge to a bound end (an earlier
@@ -253,7 +320,7 @@ gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t 
         set_error("gs_plan_query: need 1..%d patterns", kMaxPatterns);
         return GS_EINVAL;
     }
-    if ((flags & ~(GS_PLAN_DIRECTION | GS_PLAN_LISTS)) != 0) { set_error("gs_plan_query: unknown flags %u", flags); return GS_EINVAL; }
+    if ((flags & ~(GS_PLAN_DIRECTION | GS_PLAN_LISTS | GS_PLAN_PATHS)) != 0) { set_error("gs_plan_query: unknown flags %u", flags); return GS_EINVAL; }
     const uint32_t N = g ? g->N : 0xffffffffu, NP = g ? g->P : 65535u;
     int k = 0;
     std::vector<char> used(kMaxVars + 1, 0);
@@ -289,6 +356,7 @@ gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t 
     else degree_driven(G, groups, roots);
     for (auto& gr : groups) P->groups.push_back({G.V[gr.first].code(), gr.second});
     for (int r : roots) P->roots.push_back(G.V[r].code());
+    make_paths(G, groups, roots, P);
 
     // ---- schedule ----
     auto var_of = [&](int64_t x) { return x < 0 ? (int)(-x - 1) : -1; };
@@ -342,6 +410,7 @@ gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t 
         std::memset(&L, 0, sizeof(L));
         int w = order[l];
         L.var = w;
+        L.vec = l;
         for (uint32_t i = 0; i < n; ++i) {
             int64_t s = pat[3 * i], o = pat[3 * i + 2];
             uint32_t p = (uint32_t)pat[3 * i + 1];
@@ -458,6 +527,32 @@ gs_status make_plan(const gs_graph* g, const int64_t* pat, uint32_t n, uint32_t 
             P->levels[l].n_probes = 0;
         }
         if ((flags & GS_PLAN_LISTS) && P->list_ok) switch_frontier_form(P);
+    }
+    if (flags & GS_PLAN_PATHS) {
+        // per-path trees test every step against its variable's candidate
+        // vector: one vector per variable (vector v for variable v)
+        ScanSpec& S = P->path_scan;
+        std::memset(&S, 0, sizeof(S));
+        auto slot = [&](uint32_t* preds, int32_t& cnt, uint32_t p) -> int {
+            for (int j = 0; j < cnt; ++j) if (preds[j] == p) return j;
+            if (cnt >= kMaxSlots) return -1;
+            preds[cnt] = p;
+            return cnt++;
+        };
+        for (int v = 0; v < k; ++v) {
+            S.bvar[v] = v;
+            S.blevel[v] = v;
+            S.n_bvars = v + 1;
+            for (uint32_t i = 0; i < n; ++i) {
+                const int a = var_of(pat[3 * i]), b = var_of(pat[3 * i + 2]);
+                const uint32_t p = (uint32_t)pat[3 * i + 1];
+                int sl = 0;
+                if (a == v && (sl = slot(S.out_pred, S.n_out, p)) >= 0) S.need_out[v] |= 1u << sl;
+                if (a == v && sl < 0) { delete P; set_error("gs_plan_query: more than %d distinct out-predicates", kMaxSlots); return GS_ENOTIMPL; }
+                if (b == v && (sl = slot(S.in_pred, S.n_in, p)) >= 0) S.need_in[v] |= 1u << sl;
+                if (b == v && sl < 0) { delete P; set_error("gs_plan_query: more than %d distinct in-predicates", kMaxSlots); return GS_ENOTIMPL; }
+            }
+        }
     }
     *out = P;
     return GS_OK;

@@ -154,3 +154,72 @@ def test_scan_output_is_checked_before_any_native_call(monkeypatch, bad):
         g.scan([1], [0], out=out)
     with pytest.raises(ValueError):
         g.scan_noalloc([1], [0], out)
+
+
+def _oracle_paths(pats, fn):
+    """The oracle planner's Sec. 7.1 paths as variable lists, with the
+    engine's two additions: a variable's group that no walk from a root
+    enters (a constant's edge reached it first) starts paths of its own,
+    after the roots', and a variable no path holds is a path of its own."""
+    groups, roots = fn(pats)
+    starts = list(roots)
+    got = oplanner.paths(pats, groups, starts)
+    while True:   # one more start at a time, in group order
+        entered = set(starts) | {p[i] for p in got for i in range(len(p) - 1)}
+        extra = [v for v, _ in groups if v[0] == "v" and v not in entered]
+        if not extra:
+            break
+        starts.append(extra[0])
+        got = oplanner.paths(pats, groups, starts)
+    out = [[x[1] for x in p] for p in got]
+    assert all(x[0] == "v" for p in got for x in p)
+    k = 1 + max(-x - 1 for t in pats for x in (t[0], t[2]) if x < 0)
+    covered = {v for p in out for v in p}
+    out += [[v] for v in range(k) if v not in covered]
+    return out
+
+
+@pytest.mark.parametrize("flags,fn", [(0, oplanner.degree_driven), (1, oplanner.direction_driven)])
+def test_paths_match_oracle_planner(flags, fn):
+    rng = np.random.default_rng(31 + flags)
+    checked = 0
+    for _ in range(400):
+        k = int(rng.integers(1, 7))
+        n = int(rng.integers(1, 9))
+        pats = []
+        for _ in range(n):
+            ends = [int(rng.integers(0, 20)) if rng.random() < 0.15 else -int(rng.integers(0, k)) - 1
+                    for _ in range(2)]
+            pats.append((ends[0], int(rng.integers(1, 5)), ends[1]))
+        pats = [t for t in pats if t[0] != t[2]]   # self-loops: pinned by hand below
+        used = sorted({-x - 1 for t in pats for x in (t[0], t[2]) if x < 0})
+        if not used:
+            continue
+        remap = {v: i for i, v in enumerate(used)}
+        pats = [(-(remap[-a - 1]) - 1 if a < 0 else a, p, -(remap[-b - 1]) - 1 if b < 0 else b)
+                for a, p, b in pats]
+        rc, plan = _plan_nograph(pats, flags)
+        assert rc == 0
+        assert plan.paths() == _oracle_paths(pats, fn), pats
+        checked += 1
+    assert checked > 300
+
+
+@pytest.mark.parametrize("pats,want", [
+    # a path ends at a variable whose group holds only a self-loop
+    ([(-2, 1, -2), (-1, 2, -2), (-1, 1, -1), (1, 2, -3)], [[0, 1], [2]]),
+    # a self-loop counts toward the degree (x1 is the root) but is no step
+    ([(-1, 1, -2), (-2, 2, -2), (-2, 3, -3)], [[1, 0], [1, 2]]),
+    # two edges between one pair are two paths
+    ([(-1, 3, -2), (-2, 3, -1)], [[0, 1], [0, 1]]),
+])
+def test_paths_with_self_loops_and_parallel_edges(pats, want):
+    _, p = _plan_nograph(pats, 0)
+    assert p.paths() == want
+
+
+def test_paths_example_7_1():
+    """Ex. 7.1 (Fig. 2b, degree-driven): paths v2->v1, v2->v3, v2->v0->v1."""
+    pats = [(-1, 1, -2), (-1, 2, -3), (-3, 3, -2), (-4, 4, -3)]
+    _, p = _plan_nograph(pats, 0)
+    assert sorted(p.paths()) == sorted([[2, 1], [2, 0, 1], [2, 3]])
