@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(kThreads) k_range(ExecDev E, int l, LevelSpec 
         return;
     }
     const bool dead = ctl->dead != 0;
-    const uint32_t sh = pow2_shift(np, gridDim.x);
-    const uint64_t beg = min((uint64_t)blockIdx.x << sh, np), end = min(beg + ((uint64_t)1 << sh), np);
+    const uint32_t ch = even_chunk(np, gridDim.x);
+    const uint64_t beg = min((uint64_t)blockIdx.x * ch, np), end = min(beg + ch, np);
     uint64_t carry = 0;
     for (uint64_t base = beg; base < end; base += kThreads) {
         const uint64_t i = base + threadIdx.x;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kThreads) k_range(ExecDev E, int l, LevelSpec 
         }
         carry += t;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->roff_shift = sh;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->roff_chunk = ch;
     arrive_and_scan(ctl, carry, &ctl->cand);
 }
 
@@ -135,11 +135,12 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
     Ctl* ctl = E.ctl;
     if (overflowed(ctl)) return;
     __shared__ uint64_t tile_nodes[2];
+    __shared__ uint64_t roff_s[kExpTileNodes];
     const uint64_t np = l == 0 ? 1 : ctl->n[l - 1];
     const uint32_t nbm = L.n_binders > 0 ? L.n_binders : 1;
     Scratch S = scratch_at(E, np, nbm);
     const uint64_t T = ctl->cand;
-    const uint32_t sh = ctl->roff_shift;
+    const uint32_t ch = ctl->roff_chunk;
     uint64_t base_l = kCtlBytes;
     for (int j = 0; j < l; ++j) base_l += align256(8ull * ctl->n[j]);
     const uint64_t cap = S.base > base_l ? (S.base - base_l) / 8 : 0;
@@ -148,19 +149,37 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
     for (uint64_t t0 = (uint64_t)blockIdx.x * kExpTile; t0 < T; t0 += (uint64_t)gridDim.x * kExpTile) {
         uint64_t t1 = min(t0 + kExpTile, T);
         if (threadIdx.x == 0) {
-            tile_nodes[0] = upper_bound_roff(S.roff, ctl, sh, 0, np, t0) - 1;
-            tile_nodes[1] = upper_bound_roff(S.roff, ctl, sh, tile_nodes[0], np, t1 - 1);
+            tile_nodes[0] = upper_bound_roff(S.roff, ctl, ch, 0, np, t0) - 1;
+            tile_nodes[1] = upper_bound_roff(S.roff, ctl, ch, tile_nodes[0], np, t1 - 1);
         }
         __syncthreads();
         const uint64_t i0 = tile_nodes[0], i1 = tile_nodes[1];
+        // the tile's node offsets in shared memory (when they fit): the
+        // candidate -> node search then runs there
+        const bool local = i1 - i0 <= kExpTileNodes;
+        if (local)
+            for (uint64_t k = threadIdx.x; k < i1 - i0; k += kThreads)
+                roff_s[k] = roff_at(S.roff, ctl, ch, i0 + k);
+        __syncthreads();
         for (int k = 0; k < kExpItems; ++k) {
             uint64_t q = t0 + (uint64_t)k * kThreads + threadIdx.x;
             bool keep = false;
             uint32_t x = 0, node = 0;
             if (q < t1) {
-                uint64_t i = upper_bound_roff(S.roff, ctl, sh, i0, i1, q) - 1;
+                uint64_t i, j;
+                if (local) {
+                    uint32_t lo = 0, hi = (uint32_t)(i1 - i0);   // last k with roff_s[k] <= q
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (roff_s[mid] <= q) lo = mid; else hi = mid;
+                    }
+                    i = i0 + lo;
+                    j = q - roff_s[lo];
+                } else {
+                    i = upper_bound_roff(S.roff, ctl, ch, i0, i1, q) - 1;
+                    j = q - roff_at(S.roff, ctl, ch, i);
+                }
                 node = (uint32_t)i;
-                uint64_t j = q - roff_at(S.roff, ctl, sh, i);
                 uint32_t sel = S.sel[i];
                 const uint2* rng = S.rng + i * nbm;
                 if (L.src == kSrcList) {
@@ -252,8 +271,8 @@ __global__ void __launch_bounds__(kThreads) k_enum_range(ExecDev E, int last, En
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->status, kStOverflow);
         return;
     }
-    const uint32_t sh = pow2_shift(n, gridDim.x);
-    const uint64_t beg = min((uint64_t)blockIdx.x << sh, n), end = min(beg + ((uint64_t)1 << sh), n);
+    const uint32_t ch = even_chunk(n, gridDim.x);
+    const uint64_t beg = min((uint64_t)blockIdx.x * ch, n), end = min(beg + ch, n);
     uint64_t carry = 0;
     for (uint64_t base = beg; base < end; base += kThreads) {
         const uint64_t i = base + threadIdx.x;
@@ -275,7 +294,7 @@ __global__ void __launch_bounds__(kThreads) k_enum_range(ExecDev E, int last, En
         if (i < end) S.roff[i] = carry + ex;
         carry += t;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->roff_shift = sh;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->roff_chunk = ch;
     arrive_and_scan(ctl, carry, &ctl->rows);
 }
 
@@ -299,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
     const uint32_t nl = F.n_leaves > 0 ? F.n_leaves : 1;
     Scratch S = scratch_at(E, n, nl);
     const uint64_t T = ctl->rows;
-    const uint32_t sh = ctl->roff_shift;
+    const uint32_t ch = ctl->roff_chunk;
     uint64_t out_off = kCtlBytes;
     for (int j = 0; j <= last; ++j) out_off += align256(8ull * ctl->n[j]);
     const uint32_t nv = (uint32_t)F.n_vars;
@@ -315,8 +334,8 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
     for (uint64_t t0 = (uint64_t)blockIdx.x * tile_rows; t0 < T; t0 += (uint64_t)gridDim.x * tile_rows) {
         const uint64_t t1 = min(t0 + tile_rows, T);
         if (threadIdx.x == 0) {
-            tile_nodes[0] = upper_bound_roff(S.roff, ctl, sh, 0, n, t0) - 1;
-            tile_nodes[1] = upper_bound_roff(S.roff, ctl, sh, tile_nodes[0], n, t1 - 1);
+            tile_nodes[0] = upper_bound_roff(S.roff, ctl, ch, 0, n, t0) - 1;
+            tile_nodes[1] = upper_bound_roff(S.roff, ctl, ch, tile_nodes[0], n, t1 - 1);
         }
         __syncthreads();
         const uint64_t i0 = tile_nodes[0], i1 = tile_nodes[1];
@@ -325,7 +344,7 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
         const bool local = i1 - i0 <= kEnumTileNodes;
         if (local)
             for (uint64_t k = threadIdx.x; k < i1 - i0; k += kThreads)
-                roff_s[k] = roff_at(S.roff, ctl, sh, i0 + k);
+                roff_s[k] = roff_at(S.roff, ctl, ch, i0 + k);
         __syncthreads();
         for (uint64_t q = t0 + threadIdx.x; q < t1; q += kThreads) {
             uint64_t i, base;
@@ -338,8 +357,8 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
                 i = i0 + lo;
                 base = roff_s[lo];
             } else {
-                i = upper_bound_roff(S.roff, ctl, sh, i0, i1, q) - 1;
-                base = roff_at(S.roff, ctl, sh, i);
+                i = upper_bound_roff(S.roff, ctl, ch, i0, i1, q) - 1;
+                base = roff_at(S.roff, ctl, ch, i);
             }
             uint64_t loc = q - base;
             // straight into the staged row: each level's and leaf's column

@@ -19,7 +19,7 @@ struct Ctl {
     uint32_t status;               // kSt* bits
     uint32_t dead;                 // a pattern with two constant ends has no match
     uint32_t arrive;               // blocks of the running count kernel that are done
-    uint32_t roff_shift;           // its blocks took 2^roff_shift consecutive items each
+    uint32_t roff_chunk;           // its blocks took roff_chunk consecutive items each
     uint32_t levels_done;          // single-block kernel: complete levels when it handed back
     uint32_t pad;
     uint64_t bsum[kBlocks];

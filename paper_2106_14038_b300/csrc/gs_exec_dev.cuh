@@ -108,6 +108,7 @@ __device__ __forceinline__ void append(Ctl* ctl, int l, uint2* dst, uint64_t cap
 
 constexpr int kExpItems = 8;                         // candidates per thread per tile
 constexpr uint64_t kExpTile = (uint64_t)kThreads * kExpItems;
+constexpr uint32_t kExpTileNodes = 2048;             // node offsets of a tile kept in shared memory
 
 __device__ __forceinline__ uint64_t upper_bound_u64(const uint64_t* a, uint64_t lo, uint64_t hi,
                                                     uint64_t key) {
@@ -131,13 +132,13 @@ __device__ __forceinline__ void chain_done() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Count kernels split n items into blocks of 2^shift consecutive items (a
-// power of two: a consumer finds an item's block with a shift).
-__device__ __forceinline__ uint32_t pow2_shift(uint64_t n, uint32_t nb) {
-    const uint64_t chunk = (n + nb - 1) / nb;
-    uint32_t s = 0;
-    while ((1ull << s) < chunk) ++s;
-    return s;
+// Count kernels split n items (n <= 2^32) into nb chunks of `chunk`
+// consecutive items, one per block (the last ones shorter or empty), so
+// every block of the grid has work; a consumer finds an item's chunk by a
+// 32-bit division.
+__device__ __forceinline__ uint32_t even_chunk(uint64_t n, uint32_t nb) {
+    const uint64_t c = (n + nb - 1) / nb;
+    return c > 0 ? (uint32_t)c : 1u;
 }
 
 // End of a count kernel, called by every thread of every block: the block
@@ -172,18 +173,18 @@ __device__ __forceinline__ void arrive_and_scan(Ctl* ctl, uint64_t block_total, 
 
 // Global exclusive offset of item i of a count kernel's output: its offset
 // within its block plus the block's offset.
-__device__ __forceinline__ uint64_t roff_at(const uint64_t* roff, const Ctl* ctl, uint32_t sh,
+__device__ __forceinline__ uint64_t roff_at(const uint64_t* roff, const Ctl* ctl, uint32_t chunk,
                                             uint64_t i) {
-    return roff[i] + ctl->boff[i >> sh];
+    return roff[i] + ctl->boff[(uint32_t)i / chunk];
 }
 
 // First i in [lo, hi) with roff_at(i) > key (hi when none).
 __device__ __forceinline__ uint64_t upper_bound_roff(const uint64_t* roff, const Ctl* ctl,
-                                                     uint32_t sh, uint64_t lo, uint64_t hi,
+                                                     uint32_t chunk, uint64_t lo, uint64_t hi,
                                                      uint64_t key) {
     while (lo < hi) {
         const uint64_t mid = lo + ((hi - lo) >> 1);
-        if (roff_at(roff, ctl, sh, mid) <= key) lo = mid + 1; else hi = mid;
+        if (roff_at(roff, ctl, chunk, mid) <= key) lo = mid + 1; else hi = mid;
     }
     return lo;
 }

@@ -414,48 +414,147 @@ __global__ void k_scan_zero(const uint2* __restrict__ items_out, uint32_t n_out,
 
 // Candidate bits: vertex v is in vector j when its row holds every
 // out-predicate and its column every in-predicate the vector needs
-// (Eq. 21). A warp takes 256 vertices at a time, eight per lane (16-byte
-// loads of both masks: one each for 16-bit masks, two for 32-bit ones);
-// the bytes of 4 lanes are ORed into one word of each vector.
-template <typename MaskT>
-__global__ void k_scan_eval(const MaskT* __restrict__ mask_out, const MaskT* __restrict__ mask_in,
-                            uint32_t N, EvalArgs ea, uint32_t words) {
-    asm volatile("griddepcontrol.wait;" ::: "memory");   // the masks of k_scan
-    const uint32_t lane = lane_id();
-    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-    constexpr uint32_t kLoads = sizeof(MaskT) / 2;   // 16-byte loads per mask per lane
-    for (uint32_t g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g * 256 < N; g += warps) {
-        const uint32_t v = g * 256 + lane * 8;   // masks hold N + 256 slots: the loads stay inside
-        uint32_t mo[8], mi[8];
+// (Eq. 21). The test is done bit-sliced: a warp takes 1,024 vertices, 32
+// consecutive ones per lane; the lane transposes its 32 masks (a 32 x 32
+// bit matrix: one mask per row) into one word per predicate slot whose bit
+// j is vertex j's slot bit, and a vector's word is then the AND of the
+// slot words it needs. So a vector costs one AND per needed slot per 32
+// vertices, and the 32 lanes of a warp write 128 consecutive bytes of it.
+// 16-bit masks are packed two to a word (out low, in high) and transposed
+// together; 32-bit masks are transposed one direction at a time.
+constexpr uint32_t kEvalThreads = 128;
+
+// In-place transpose of a 32 x 32 bit matrix (a[j] bit s -> a[s] bit j):
+// exchange the off-diagonal halves of every 2w x 2w block, for w = 16, 8,
+// 4, 2, 1 (each step swaps bits (j + w, s) and (j, s + w) of the blocks'
+// rows through an XOR difference).
+__device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
 #pragma unroll
-        for (uint32_t h = 0; h < kLoads; ++h) {
-            const uint4 a = __ldcs(reinterpret_cast<const uint4*>(mask_out + v) + h);
-            const uint4 b = __ldcs(reinterpret_cast<const uint4*>(mask_in + v) + h);
-            const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+    for (int w = 16; w >= 1; w >>= 1) {
+        const uint32_t m = w == 16 ? 0x0000ffffu
+                         : w == 8  ? 0x00ff00ffu
+                         : w == 4  ? 0x0f0f0f0fu
+                         : w == 2  ? 0x33333333u
+                                   : 0x55555555u;
 #pragma unroll
-            for (uint32_t k = 0; k < 4; ++k) {
-                if constexpr (sizeof(MaskT) == 2) {   // word k: vertices v + 2k (low), v + 2k + 1
-                    mo[2 * k] = aw[k] & 0xffffu; mo[2 * k + 1] = aw[k] >> 16;
-                    mi[2 * k] = bw[k] & 0xffffu; mi[2 * k + 1] = bw[k] >> 16;
-                } else {                              // word k of load h: vertex v + 4h + k
-                    mo[4 * h + k] = aw[k];
-                    mi[4 * h + k] = bw[k];
-                }
-            }
-        }
-        for (uint32_t j = 0; j < ea.n; ++j) {
-            const EvalVec e = ea.list ? ea.list[j] : ea.inl[j];
-            uint32_t byte = 0;
-#pragma unroll
-            for (uint32_t k = 0; k < 8; ++k)
-                byte |= (uint32_t)(eval_bit(e, mo[k], mi[k]) && v + k < N) << k;
-            uint32_t word = byte << (8 * (lane & 3));
-            word |= __shfl_xor_sync(0xffffffffu, word, 1);
-            word |= __shfl_xor_sync(0xffffffffu, word, 2);
-            const uint32_t wi = g * 8 + (lane >> 2);
-            if ((lane & 3) == 0 && wi < words) e.dst[wi] = word;
+        for (int j = 0; j < 32; ++j) {
+            if (j & w) continue;
+            const uint32_t t = ((a[j] >> w) ^ a[j + w]) & m;
+            a[j + w] ^= t;
+            a[j] ^= t << w;
         }
     }
+}
+
+// The 32 masks of vertices base..base+31 into a[] (16-bit masks: out in the
+// low, in in the high half of each word; 32-bit masks: the one array m).
+// Lanes past N load nothing; a lane that runs past N reads at most 31 slots
+// past it (the mask arrays hold N + 256).
+__device__ __forceinline__ void load_masks16(const uint16_t* __restrict__ mo,
+                                             const uint16_t* __restrict__ mi, uint32_t base,
+                                             uint32_t N, uint32_t (&a)[32]) {
+    if (base >= N) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a[j] = 0;
+        return;
+    }
+    const uint4* po = reinterpret_cast<const uint4*>(mo + base);
+    const uint4* pi = reinterpret_cast<const uint4*>(mi + base);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const uint4 x = __ldcs(po + h), y = __ldcs(pi + h);
+        const uint32_t xo[4] = {x.x, x.y, x.z, x.w}, yi[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {   // word k: vertices 8h + 2k (low half) and 8h + 2k + 1
+            a[8 * h + 2 * k] = (xo[k] & 0xffffu) | (yi[k] << 16);
+            a[8 * h + 2 * k + 1] = (xo[k] >> 16) | (yi[k] & 0xffff0000u);
+        }
+    }
+}
+
+__device__ __forceinline__ void load_masks32(const uint32_t* __restrict__ m, uint32_t base,
+                                             uint32_t N, uint32_t (&a)[32]) {
+    if (base >= N) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a[j] = 0;
+        return;
+    }
+    const uint4* p = reinterpret_cast<const uint4*>(m + base);
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+        const uint4 x = __ldcs(p + h);
+        a[4 * h] = x.x;
+        a[4 * h + 1] = x.y;
+        a[4 * h + 2] = x.z;
+        a[4 * h + 3] = x.w;
+    }
+}
+
+template <typename MaskT>
+__global__ void __launch_bounds__(kEvalThreads) k_scan_eval(const MaskT* __restrict__ mask_out,
+                                                            const MaskT* __restrict__ mask_in,
+                                                            uint32_t N, EvalArgs ea, uint32_t words) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the masks of k_scan
+    constexpr bool kNarrow = sizeof(MaskT) == 2;
+    constexpr uint32_t kRows = kNarrow ? 32 : 64;        // slot words per lane
+    constexpr uint32_t kInRow = kNarrow ? 16 : 32;       // first in-slot word
+    // slot word s of lane l at sw[s][l]: each lane reads back only its own
+    // column (a dynamically indexed register file), without bank conflicts
+    __shared__ uint32_t sw_all[kEvalThreads / 32][kRows][32];
+    uint32_t (*sw)[32] = sw_all[threadIdx.x >> 5];
+    const uint32_t lane = lane_id();
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); (uint64_t)c * 1024 < N;
+         c += warps) {
+        const uint32_t base = c * 1024 + lane * 32;
+        const uint32_t valid = base >= N ? 0u : N - base >= 32 ? 0xffffffffu : (1u << (N - base)) - 1u;
+        uint32_t a[32];
+        if constexpr (kNarrow) {
+            load_masks16(mask_out, mask_in, base, N, a);
+            transpose32(a);
+#pragma unroll
+            for (int s = 0; s < 32; ++s) sw[s][lane] = a[s];
+        } else {
+            load_masks32(mask_out, base, N, a);
+            transpose32(a);
+#pragma unroll
+            for (int s = 0; s < 32; ++s) sw[s][lane] = a[s];
+            load_masks32(mask_in, base, N, a);
+            transpose32(a);
+#pragma unroll
+            for (int s = 0; s < 32; ++s) sw[32 + s][lane] = a[s];
+        }
+        const uint32_t wi = c * 32 + lane;
+        for (uint32_t j = 0; j < ea.n; ++j) {
+            const EvalVec e = ea.list ? ea.list[j] : ea.inl[j];
+            uint32_t acc = valid;
+            for (uint32_t m = e.need_out; m; m &= m - 1) acc &= sw[__ffs(m) - 1][lane];
+            for (uint32_t m = e.need_in; m; m &= m - 1) acc &= sw[kInRow + __ffs(m) - 1][lane];
+            if (wi < words) e.dst[wi] = acc;
+        }
+    }
+}
+
+// Blocks of k_scan_eval that fit on one SM at once (asked once per device
+// and mask width): the grid is one wave of them, so no block starts late.
+// Per-device launch facts below share one mutex.
+constexpr int kAttrDevices = 64;
+static std::mutex g_attr_mu;
+static int g_eval_fit[kAttrDevices][2];
+
+template <typename MaskT>
+static int eval_blocks_per_sm(int dev) {
+    if (dev < 0 || dev >= kAttrDevices) return 1;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    int& fit = g_eval_fit[dev][sizeof(MaskT) == 2 ? 0 : 1];
+    if (fit <= 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_scan_eval<MaskT>, kEvalThreads, 0) !=
+                cudaSuccess || n <= 0)
+            n = 1;
+        fit = n;
+    }
+    return fit;
 }
 
 // Workspace: mask_out | mask_in (N + 256 slots of 16 or 32 bits each,
@@ -480,9 +579,7 @@ long long scan_stall_cycles() {
 }
 
 // Dynamic shared memory already allowed for each k_scan variant on each
-// device (function attributes are per device); guarded by one mutex.
-constexpr int kAttrDevices = 64;
-static std::mutex g_attr_mu;
+// device (function attributes are per device); guarded by g_attr_mu.
 static size_t g_smem_set[kAttrDevices][4];
 
 template <typename LutT, typename MaskT>
@@ -562,14 +659,17 @@ gs_status scan_masks(const gs_graph* g, const uint32_t* out_pred, uint32_t n_out
 gs_status scan_eval(const gs_graph* g, const void* work, bool wide, const EvalArgs& ea,
                     cudaStream_t st) {
     const uint32_t words = (g->N + 31) / 32;
-    const uint32_t eb = std::min<uint32_t>((words + 63) / 64, (uint32_t)g->sm_count * 8);
+    const uint32_t chunks = (uint32_t)(((uint64_t)g->N + 1023) / 1024);
+    const uint32_t want = std::max(1u, (chunks + kEvalThreads / 32 - 1) / (kEvalThreads / 32));
+    const int fit = wide ? eval_blocks_per_sm<uint32_t>(g->device) : eval_blocks_per_sm<uint16_t>(g->device);
+    const uint32_t eb = std::min<uint32_t>(want, (uint32_t)g->sm_count * (uint32_t)fit);
     if (wide) {
         const uint32_t* mo = (const uint32_t*)work;
-        GS_CUDA(launch_chained(k_scan_eval<uint32_t>, dim3(std::max(1u, eb)), dim3(kThreads), 0, st,
+        GS_CUDA(launch_chained(k_scan_eval<uint32_t>, dim3(eb), dim3(kEvalThreads), 0, st,
                                mo, mo + mask_slots(g->N), g->N, ea, words));
     } else {
         const uint16_t* mo = (const uint16_t*)work;
-        GS_CUDA(launch_chained(k_scan_eval<uint16_t>, dim3(std::max(1u, eb)), dim3(kThreads), 0, st,
+        GS_CUDA(launch_chained(k_scan_eval<uint16_t>, dim3(eb), dim3(kEvalThreads), 0, st,
                                mo, mo + mask_slots(g->N), g->N, ea, words));
     }
     GS_CUDA(cudaGetLastError());
