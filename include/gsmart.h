@@ -167,6 +167,23 @@ gs_status gs_plan_paths(const gs_plan* plan, int32_t* buf, uint32_t cap, uint32_
  * device memory until gs_free_result. */
 gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_result** out);
 
+/* Root-range evaluation: the first-stage partition of Sec. 6.3.1. Every
+ * answer has exactly one binding of the plan's root variable (the variable
+ * of its first level, gs_plan_root), so evaluating the query once per
+ * range of a partition of the vertex ids [0, N) and concatenating the
+ * answers gives the whole answer set, each row once; replicas each holding
+ * the full graph can take one range apiece and exchange only the answers
+ * at the end. gs_eval_query_roots returns the answers of plan whose root
+ * binding lies in [root_lo, root_hi) (root_hi may exceed N; an empty range
+ * gives no answers). It runs on the grid path (the root filter sits in the
+ * level-0 kernels); the result is used and freed like gs_eval_query's.
+ * GS_EINVAL for NULL arguments, root_lo > root_hi, or a GS_PLAN_PATHS plan
+ * (one root per path). gs_plan_root writes the root variable's index (its
+ * answer column); GS_EINVAL for a GS_PLAN_PATHS plan. Host only. */
+gs_status gs_eval_query_roots(gs_graph* g, const gs_plan* plan, uint32_t root_lo, uint32_t root_hi,
+                              void* cuda_stream, gs_result** out);
+gs_status gs_plan_root(const gs_plan* plan, uint32_t* var);
+
 /* Estimated device memory of evaluating the plan alone on g (*bytes: the
  * binding-tree levels of Sec. 7.1 with their scratch, the answer rows, and
  * for a plan with a triple scan its candidate vectors and masks) and its

@@ -39,7 +39,7 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_plan_estimate", "gs_server_ticket", "gs_server_admission",
             "gs_server_submit_many", "gs_lspm_build", "gs_lspm_for_plan", "gs_lspm_info",
             "gs_lspm_export", "gs_eval_query_lspm", "gs_free_lspm", "gs_server_work",
-            "gs_result_tree", "gs_plan_paths"]
+            "gs_result_tree", "gs_plan_paths", "gs_eval_query_roots", "gs_plan_root"]
 
 
 class GsError(RuntimeError):
@@ -135,6 +135,8 @@ def load_library(path: str | None = None):
         "gs_plan_describe": [vp, vp, u32, P(u32)],
         "gs_plan_paths": [vp, vp, u32, P(u32)],
         "gs_eval_query": [vp, vp, vp, P(vp)],
+        "gs_eval_query_roots": [vp, vp, u32, u32, vp, P(vp)],
+        "gs_plan_root": [vp, P(u32)],
         "gs_result_info": [vp, P(u64), P(u32)],
         "gs_fetch_bindings": [vp, vp, u64, i32, i32],
         "gs_result_stats": [vp, P(ctypes.c_float), P(u32)],
@@ -264,10 +266,17 @@ class Graph:
     def plan(self, patterns, flags: int = PLAN_DEGREE) -> "Plan":
         return Plan(self, patterns, flags)
 
-    def eval(self, plan_or_patterns, stream=None) -> "Result":
+    def eval(self, plan_or_patterns, stream=None, roots=None) -> "Result":
+        """Evaluate a plan; with roots=(lo, hi) only the answers whose root
+        binding (column plan.root_var) lies in [lo, hi)."""
         plan = plan_or_patterns if isinstance(plan_or_patterns, Plan) else self.plan(plan_or_patterns)
         h = ctypes.c_void_p()
-        _check(_lib.gs_eval_query(self._h, plan._h, _stream_handle(stream), ctypes.byref(h)))
+        if roots is None:
+            _check(_lib.gs_eval_query(self._h, plan._h, _stream_handle(stream), ctypes.byref(h)))
+        else:
+            lo, hi = (int(x) for x in roots)
+            _check(_lib.gs_eval_query_roots(self._h, plan._h, lo, hi, _stream_handle(stream),
+                                            ctypes.byref(h)))
         return Result(h, plan)
 
     def query(self, patterns, sort: bool = True, flags: int = PLAN_DEGREE, stream=None):
@@ -443,6 +452,13 @@ class Plan:
             ends = self.patterns[:, [0, 2]]
             self._n_vars = int(-ends[ends < 0].min()) if (ends < 0).any() else 0
         return self._n_vars
+
+    @property
+    def root_var(self) -> int:
+        """The root variable (answer column) that root ranges partition."""
+        v = ctypes.c_uint32()
+        _check(_lib.gs_plan_root(self._h, ctypes.byref(v)))
+        return int(v.value)
 
     def describe(self):
         """(groups, roots): groups = [(vertex, [edge indices])]; a vertex is a

@@ -84,6 +84,8 @@ struct gs_result {
     const Store* so = nullptr;
     const Store* si = nullptr;
     bool bits_borrowed = false;   // bits belong to the caller (per-path evaluation)
+    bool root_cut = false;        // only roots in [root_lo, root_hi) (gs_eval_query_roots)
+    uint32_t root_lo = 0, root_hi = 0;
     std::vector<uint64_t> path_nodes;   // per-path mode: binding-tree nodes of each path
     uint32_t launches = 0;
     uint64_t rows = 0;
@@ -153,6 +155,9 @@ ExecDev exec_view(gs_result* r) {
     E.words = (r->g->N + 31) / 32;
     E.lists = r->lists;
     E.list_stride = r->list_stride;
+    E.root_cut = r->root_cut ? 1u : 0u;
+    E.root_lo = r->root_lo;
+    E.root_hi = r->root_hi;
     return E;
 }
 
@@ -283,6 +288,7 @@ gs_status gs_load_triples(const uint32_t* s, const uint32_t* p, const uint32_t* 
     if (alloc) { g->alloc.hook = *alloc; g->alloc.has_hook = true; }
     cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev);
     g->n_blocks = std::min(kBlocks, std::max(1, g->sm_count * 4));
+    level_grids(g->sm_count, &g->range_blocks, &g->expand_blocks);
     set_pool_threshold(dev);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     gs_status rc = build_store(g, s, p, o, n, inputs_on_device != 0, st);
@@ -524,9 +530,16 @@ gs_status gs::result_ready(gs_result* r, int* done) {
 
 namespace {
 
+// A root range of a partitioned evaluation (cut false: every root).
+struct RootCut {
+    bool cut = false;
+    uint32_t lo = 0, hi = 0;
+};
+
 gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
                           uint32_t* pre_bits, cudaEvent_t pre_ready, const uint32_t* pre_status,
-                          gs_result** out, const Store* so = nullptr, const Store* si = nullptr);
+                          gs_result** out, const Store* so = nullptr, const Store* si = nullptr,
+                          RootCut roots = RootCut());
 
 }  // namespace
 
@@ -591,7 +604,7 @@ namespace {
 
 gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, int force_grid,
                           uint32_t* pre_bits, cudaEvent_t pre_ready, const uint32_t* pre_status,
-                          gs_result** out, const Store* so, const Store* si) {
+                          gs_result** out, const Store* so, const Store* si, RootCut roots) {
     if (!g || !plan || !out) { set_error("gs_eval_query: NULL argument"); return GS_EINVAL; }
     *out = nullptr;
     if (plan->N == 0) {   // planned without a graph: check the ids now
@@ -617,6 +630,9 @@ gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, i
     r->st = (cudaStream_t)cuda_stream;
     r->so = so;
     r->si = si;
+    r->root_cut = roots.cut;
+    r->root_lo = roots.lo;
+    r->root_hi = roots.hi;
     const uint64_t words = (g->N + 31) / 32;
     gs_status rc = GS_OK;
     cudaEvent_t* ev[3] = {&r->ev0, &r->ev1, &r->ev2};
@@ -646,7 +662,9 @@ gs_status eval_query_impl(gs_graph* g, const gs_plan* plan, void* cuda_stream, i
     plan_estimate(g, plan, &est);
     bool big = est.rows > kSmallRows;
     for (int l = 0; l < plan->n_levels; ++l) big |= est.nodes[l] > kSmallNodes;
-    r->mode = (small_eligible(plan) && !force_grid && !big && first_level_bound(g, plan) <= kSmallRoute) ? 1 : 0;
+    // (a root range is applied by the grid path's level-0 kernels only)
+    r->mode = (small_eligible(plan) && !force_grid && !roots.cut && !big &&
+               first_level_bound(g, plan) <= kSmallRoute) ? 1 : 0;
     if (rc == GS_OK) {
         // the grid path's size for both: a query the single-CTA kernel hands
         // back continues in this workspace
@@ -669,6 +687,36 @@ gs_status gs_eval_query(gs_graph* g, const gs_plan* plan, void* cuda_stream, gs_
     if (plan && (plan->flags & GS_PLAN_PATHS)) return eval_paths(g, plan, cuda_stream, out);
     const char* how = getenv("GS_EXEC");   // "grid" forces the grid path
     return eval_query_path(g, plan, cuda_stream, how && !strcmp(how, "grid"), out);
+}
+
+gs_status gs_eval_query_roots(gs_graph* g, const gs_plan* plan, uint32_t root_lo, uint32_t root_hi,
+                              void* cuda_stream, gs_result** out) {
+    if (out) *out = nullptr;
+    if (!g || !plan || !out) { set_error("gs_eval_query_roots: NULL argument"); return GS_EINVAL; }
+    if (plan->flags & GS_PLAN_PATHS) {
+        set_error("gs_eval_query_roots: a per-path plan has one root per path; plan without GS_PLAN_PATHS");
+        return GS_EINVAL;
+    }
+    if (root_lo > root_hi) {
+        set_error("gs_eval_query_roots: root_lo %u > root_hi %u", root_lo, root_hi);
+        return GS_EINVAL;
+    }
+    RootCut c;
+    c.cut = true;
+    c.lo = root_lo;
+    c.hi = root_hi;
+    return eval_query_impl(g, plan, cuda_stream, 1, nullptr, nullptr, nullptr, out, nullptr, nullptr, c);
+}
+
+gs_status gs_plan_root(const gs_plan* plan, uint32_t* var) {
+    if (!plan || !var) { set_error("gs_plan_root: NULL argument"); return GS_EINVAL; }
+    if (plan->flags & GS_PLAN_PATHS) {
+        set_error("gs_plan_root: a per-path plan has one root per path");
+        return GS_EINVAL;
+    }
+    if (plan->n_levels < 1) { set_error("gs_plan_root: the plan has no level"); return GS_EINVAL; }
+    *var = (uint32_t)plan->levels[0].var;
+    return GS_OK;
 }
 
 }  // extern "C"

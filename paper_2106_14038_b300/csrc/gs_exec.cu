@@ -78,7 +78,7 @@ __global__ void k_resume(ExecDev E, int from) {
 
 // Candidate counts of the parent nodes of level l, as block-local
 // exclusive offsets; the last block writes the block offsets and the total.
-__global__ void __launch_bounds__(kThreads) k_range(ExecDev E, int l, LevelSpec L) {
+__global__ void __launch_bounds__(kThreads, 5) k_range(ExecDev E, int l, LevelSpec L) {
     chain_enter();
     Ctl* ctl = E.ctl;
     if (overflowed(ctl)) return;
@@ -106,14 +106,29 @@ __global__ void __launch_bounds__(kThreads) k_range(ExecDev E, int l, LevelSpec 
             } else {
                 uint32_t vid[kMaxLevels];
                 if (l > 0) walk(lv, l - 1, (uint32_t)i, vid);
+                // the row bounds of every binder first (independent loads in
+                // flight together), then the label lookups
+                uint32_t row[kMaxBinders], rb[kMaxBinders], re[kMaxBinders];
+#pragma unroll
+                for (int b = 0; b < kMaxBinders; ++b) {
+                    if (b < L.n_binders) {
+                        const Binder& B = L.b[b];
+                        const DStore& D = store_of(E, B.dir);
+                        row[b] = B.from_const ? B.c : vid[B.level];
+                        rb[b] = ld(D.ptr + row[b]);
+                        re[b] = ld(D.ptr + row[b] + 1);
+                    }
+                }
                 uint32_t best = 0xffffffffu;
-                for (int b = 0; b < L.n_binders; ++b) {
-                    const Binder& B = L.b[b];
-                    uint32_t row = B.from_const ? B.c : vid[B.level];
-                    uint32_t lo, len;
-                    label_range(store_of(E, B.dir), row, B.label, lo, len);
-                    S.rng[i * nbm + b] = make_uint2(lo, len);
-                    if (len < best) { best = len; sel = (uint32_t)b; }
+#pragma unroll
+                for (int b = 0; b < kMaxBinders; ++b) {
+                    if (b < L.n_binders) {
+                        const Binder& B = L.b[b];
+                        uint32_t lo, len;
+                        label_range_in(store_of(E, B.dir), row[b], rb[b], re[b], B.label, lo, len);
+                        S.rng[i * nbm + b] = make_uint2(lo, len);
+                        if (len < best) { best = len; sel = (uint32_t)b; }
+                    }
                 }
                 cnt = best;
             }
@@ -188,7 +203,8 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
                     uint2 r = rng[sel];
                     x = __ldg(store_of(E, L.b[sel].dir).idx + r.x + j);
                 }
-                keep = keep_candidate(E, L, l, x, rng, L.src == kSrcList ? 0xffffffffu : sel);
+                keep = (l != 0 || root_ok(E, x)) &&
+                       keep_candidate(E, L, l, x, rng, L.src == kSrcList ? 0xffffffffu : sel);
             }
             append(ctl, l, dst, cap, keep, x, node);
         }
@@ -210,8 +226,10 @@ __global__ void __launch_bounds__(kThreads) k_bits_count(ExecDev E, int l, Level
     block_chunk(E.words, blockIdx.x, gridDim.x, beg, end);
     uint64_t c = 0;
     if (!E.ctl->dead)
-        for (uint64_t w = beg + threadIdx.x; w < end; w += kThreads)
-            c += __popc(word_keep(E, L, (uint32_t)w, bm[w]));
+        for (uint64_t w = beg + threadIdx.x; w < end; w += kThreads) {
+            const uint32_t word = l == 0 ? bm[w] & root_word_mask(E, (uint32_t)w) : bm[w];
+            c += __popc(word_keep(E, L, (uint32_t)w, word));
+        }
     c = block_sum_u64(c);
     arrive_and_scan(E.ctl, c, l == 0 ? &E.ctl->n[0] : &E.ctl->list_n[l]);
 }
@@ -232,7 +250,9 @@ __global__ void __launch_bounds__(kThreads) k_bits_write(ExecDev E, int l, Level
     uint64_t carry = ctl->boff[blockIdx.x];
     for (uint64_t base = beg; base < end; base += kThreads) {
         uint64_t w = base + threadIdx.x;
-        uint32_t word = w < end ? word_keep(E, L, (uint32_t)w, bm[w]) : 0u;
+        uint32_t word = 0u;
+        if (w < end)
+            word = word_keep(E, L, (uint32_t)w, to_level ? bm[w] & root_word_mask(E, (uint32_t)w) : bm[w]);
         uint64_t t;
         uint64_t pos = carry + block_excl_scan_u64(__popc(word), &t);
         for (uint32_t m = word; m; m &= m - 1) {
@@ -402,6 +422,15 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
 
 // ------------------------------------------------------------------ //
 
+void level_grids(int sm_count, int* range_blocks, int* expand_blocks) {
+    int fr = 0, fe = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fr, k_range, kThreads, 0) != cudaSuccess || fr < 1) fr = 4;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fe, k_expand, kThreads, 0) != cudaSuccess || fe < 1) fe = 4;
+    cudaGetLastError();
+    *range_blocks = std::max(1, std::min(kBlocks, sm_count * fr));
+    *expand_blocks = std::max(1, sm_count * fe);
+}
+
 uint64_t host_level_off(const uint64_t* n, int l) {
     uint64_t o = kCtlBytes;
     for (int j = 0; j < l; ++j) o += align256(8ull * n[j]);
@@ -440,8 +469,8 @@ gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, vo
             nl_launch += 2;
             if (l == 0) continue;
         }
-        GS_CUDA(launch_chained(k_range, nb, th, 0, st, E, l, L));
-        GS_CUDA(launch_chained(k_expand, nb, th, 0, st, E, l, L));
+        GS_CUDA(launch_chained(k_range, dim3(g->range_blocks), th, 0, st, E, l, L));
+        GS_CUDA(launch_chained(k_expand, dim3(g->expand_blocks), th, 0, st, E, l, L));
         nl_launch += 2;
     }
     const int last = P->n_levels - 1;

@@ -37,6 +37,9 @@ struct ExecDev {
     uint64_t words;
     uint32_t* lists;          // candidate list of level l at lists + l * list_stride
     uint64_t list_stride;
+    // root range (first-stage partition of Sec. 6.3.1): with root_cut set,
+    // level 0 keeps only vertices in [root_lo, root_hi)
+    uint32_t root_cut, root_lo, root_hi;
 };
 
 struct ConstChecks {
@@ -139,6 +142,10 @@ struct Estimate {
 void plan_estimate(const gs_graph* g, const gs_plan* P, Estimate* e);
 // The first workspace a grid-path evaluation of a plan with estimate e takes.
 uint64_t first_arena_bytes(gs_graph* g, const Estimate& e);
+
+// Grids of k_range and k_expand on a device with sm_count SMs: the blocks
+// that fit at once (k_range's at most kBlocks, the size of its block sums).
+void level_grids(int sm_count, int* range_blocks, int* expand_blocks);
 
 uint64_t host_level_off(const uint64_t* n, int l);
 bool small_eligible(const gs_plan* P);

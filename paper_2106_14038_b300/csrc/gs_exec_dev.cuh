@@ -189,6 +189,23 @@ __device__ __forceinline__ uint64_t upper_bound_roff(const uint64_t* roff, const
     return lo;
 }
 
+// Root range of a partitioned evaluation: is x a root the evaluation keeps,
+// and which bits of candidate word w (vertices 32w .. 32w + 31) are roots it
+// keeps.
+__device__ __forceinline__ bool root_ok(const ExecDev& E, uint32_t x) {
+    return !E.root_cut || (x >= E.root_lo && x < E.root_hi);
+}
+
+__device__ __forceinline__ uint32_t root_word_mask(const ExecDev& E, uint32_t w) {
+    if (!E.root_cut) return 0xffffffffu;
+    const uint64_t v0 = (uint64_t)w * 32, lo = E.root_lo, hi = E.root_hi;
+    if (v0 + 32 <= lo || v0 >= hi) return 0u;
+    uint32_t m = 0xffffffffu;
+    if (lo > v0) m &= 0xffffffffu << (uint32_t)(lo - v0);          // lo - v0 in 1..31
+    if (hi < v0 + 32) m &= (1u << (uint32_t)(hi - v0)) - 1u;       // hi - v0 in 1..31
+    return m;
+}
+
 __device__ __forceinline__ bool self_ok(const ExecDev& E, const LevelSpec& L, uint32_t x) {
     for (int j = 0; j < L.n_self; ++j) {
         uint32_t lo, len;

@@ -128,6 +128,8 @@ struct gs_graph {
     gs::Alloc alloc;
     int sm_count = 148;
     int n_blocks = 592;
+    // grids of the level kernels: as many blocks as fit on the SMs at once
+    int range_blocks = 592, expand_blocks = 592;
     int device = 0;
     // streams on which batched evaluations run their grid-path queries
     // side by side (created on first use, destroyed with the graph)

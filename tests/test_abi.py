@@ -223,3 +223,18 @@ def test_paths_example_7_1():
     pats = [(-1, 1, -2), (-1, 2, -3), (-3, 3, -2), (-4, 4, -3)]
     _, p = _plan_nograph(pats, 0)
     assert sorted(p.paths()) == sorted([[2, 1], [2, 0, 1], [2, 3]])
+
+
+def test_plan_root_and_root_range_arguments():
+    lib = gs.load_library()
+    rc, p = _plan_nograph([[-1, 1, -2], [-2, 2, -3], [-2, 3, -4]])
+    assert rc == 0
+    assert 0 <= p.root_var < 4
+    rc, pp = _plan_nograph([[-1, 1, -2], [-2, 2, -3]], gs.PLAN_PATHS)
+    assert rc == 0
+    v = ctypes.c_uint32()
+    assert lib.gs_plan_root(pp._h, ctypes.byref(v)) == 1          # GS_EINVAL: one root per path
+    assert lib.gs_plan_root(None, ctypes.byref(v)) == 1
+    h = ctypes.c_void_p(1)
+    assert lib.gs_eval_query_roots(None, p._h, 0, 10, None, ctypes.byref(h)) == 1
+    assert h.value is None                                         # *out cleared on error
