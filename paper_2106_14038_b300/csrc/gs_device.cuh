@@ -77,9 +77,9 @@ static_assert(kShort == kDirMin, "rows without a label directory are the short o
 // by (label, idx), so this is Eq. 8's S_p (x) A restricted to one row. A
 // long row is looked up in its label directory (one entry per run of equal
 // labels, at most P) instead of its whole label array.
-// label_range for a row whose bounds b = ptr[r], e = ptr[r + 1] are known.
-__device__ __forceinline__ void label_range_in(const DStore& S, uint32_t r, uint32_t b, uint32_t e,
-                                               uint32_t p, uint32_t& lo, uint32_t& len) {
+__device__ __forceinline__ void label_range(const DStore& S, uint32_t r, uint32_t p, uint32_t& lo,
+                                            uint32_t& len) {
+    const uint32_t b = ld(S.ptr + r), e = ld(S.ptr + r + 1);
     if (e - b <= kShort) {
         uint32_t below, equal;
         count_short(S.lab, b, e, p, below, equal);
@@ -103,11 +103,6 @@ __device__ __forceinline__ void label_range_in(const DStore& S, uint32_t r, uint
     const uint32_t h = lower_bound_u32(S.lab, l, e, p + 1);
     lo = l;
     len = h - l;
-}
-
-__device__ __forceinline__ void label_range(const DStore& S, uint32_t r, uint32_t p, uint32_t& lo,
-                                            uint32_t& len) {
-    label_range_in(S, r, ld(S.ptr + r), ld(S.ptr + r + 1), p, lo, len);
 }
 
 // Does row r hold predicate p (Eq. 4 for one row)?

@@ -78,7 +78,7 @@ __global__ void k_resume(ExecDev E, int from) {
 
 // Candidate counts of the parent nodes of level l, as block-local
 // exclusive offsets; the last block writes the block offsets and the total.
-__global__ void __launch_bounds__(kThreads, 5) k_range(ExecDev E, int l, LevelSpec L) {
+__global__ void __launch_bounds__(kThreads) k_range(ExecDev E, int l, LevelSpec L) {
     chain_enter();
     Ctl* ctl = E.ctl;
     if (overflowed(ctl)) return;
@@ -106,29 +106,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_range(ExecDev E, int l, LevelSp
             } else {
                 uint32_t vid[kMaxLevels];
                 if (l > 0) walk(lv, l - 1, (uint32_t)i, vid);
-                // the row bounds of every binder first (independent loads in
-                // flight together), then the label lookups
-                uint32_t row[kMaxBinders], rb[kMaxBinders], re[kMaxBinders];
-#pragma unroll
-                for (int b = 0; b < kMaxBinders; ++b) {
-                    if (b < L.n_binders) {
-                        const Binder& B = L.b[b];
-                        const DStore& D = store_of(E, B.dir);
-                        row[b] = B.from_const ? B.c : vid[B.level];
-                        rb[b] = ld(D.ptr + row[b]);
-                        re[b] = ld(D.ptr + row[b] + 1);
-                    }
-                }
                 uint32_t best = 0xffffffffu;
-#pragma unroll
-                for (int b = 0; b < kMaxBinders; ++b) {
-                    if (b < L.n_binders) {
-                        const Binder& B = L.b[b];
-                        uint32_t lo, len;
-                        label_range_in(store_of(E, B.dir), row[b], rb[b], re[b], B.label, lo, len);
-                        S.rng[i * nbm + b] = make_uint2(lo, len);
-                        if (len < best) { best = len; sel = (uint32_t)b; }
-                    }
+                for (int b = 0; b < L.n_binders; ++b) {
+                    const Binder& B = L.b[b];
+                    uint32_t row = B.from_const ? B.c : vid[B.level];
+                    uint32_t lo, len;
+                    label_range(store_of(E, B.dir), row, B.label, lo, len);
+                    S.rng[i * nbm + b] = make_uint2(lo, len);
+                    if (len < best) { best = len; sel = (uint32_t)b; }
                 }
                 cnt = best;
             }
