@@ -57,6 +57,9 @@ def _args():
                     help="batched mode: number of queries (0: the workload's)")
     ap.add_argument("--query", default="0",
                     help="query mode: comma-separated indices into the workload's queries")
+    ap.add_argument("--family", default="default", choices=["default", "bandwidth"],
+                    help="query mode: the workload's own queries, or the bandwidth family's "
+                         "copy for its graph (rdfgen/<workload>_bandwidth.txt)")
     ap.add_argument("--batch", action="store_true",
                     help="query mode: evaluate the selected queries as one batch per round")
     return ap.parse_args()
@@ -151,10 +154,10 @@ def _dist():
     return ws, rank, local
 
 
-def _workload(name):
+def _workload(name, family="default"):
     w = rdfgen.WORKLOADS[name]
     s, p, o = rdfgen.graph(w)
-    if name == "rmat26":     # the bandwidth workload's stored queries
+    if name == "rmat26" or family == "bandwidth":   # the bandwidth family's stored queries
         return w, (s, p, o), rdfgen.bandwidth_workload(w)
     sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
     qs = rdfgen.queries(w, sm)
@@ -698,7 +701,7 @@ def run_query(args):
     import torch
     torch.cuda.set_device(0)
     import paper_2106_14038_b300 as gs
-    w, triples, qs = _workload(args.workload)
+    w, triples, qs = _workload(args.workload, args.family)
     g = gs.Graph(*triples, w.n_vertices, w.n_preds)
     sel = [int(x) for x in args.query.split(",")]
     stream = torch.cuda.current_stream()
@@ -717,7 +720,8 @@ def run_query(args):
         print(json.dumps({
             "metric": "device ms per batch", "unit": "ms", "higher_is_better": False,
             "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
-            "config": {"workload": w.name, "queries": sel}, "device_ms": float(np.mean(ms)),
+            "config": {"workload": w.name, "family": args.family, "queries": sel},
+            "device_ms": float(np.mean(ms)),
             "rows": [int(x) for x in rows], "triple_scans": scans[0], "gpu_launches": launches,
         }), flush=True)
         return
@@ -744,7 +748,7 @@ def run_query(args):
     print(json.dumps({
         "metric": "device ms per query", "unit": "ms", "higher_is_better": False,
         "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
-        "config": {"workload": w.name, "queries": sel},
+        "config": {"workload": w.name, "family": args.family, "queries": sel},
         "queries": [{"index": i, "shape": info[i][0], "rows": info[i][1], "launches": info[i][2],
                      "tree_nodes": info[i][3], "estimate_bytes": info[i][4][0],
                      "estimate_rows": info[i][4][1], "device_ms": float(np.mean(dev[i]))}

@@ -260,9 +260,11 @@ typedef struct {
     uint32_t scan_share;     /* triple scans of the plans that need one
                                 (constant-free plans): 0 or 1, shared: plans
                                 are packed into passes of at most 32
-                                predicates per direction and each pass reads
-                                the labels once (Sec. 5 grouping applied
-                                across queries); 2, one scan per plan */
+                                predicates per direction (each plan into the
+                                pass it adds the fewest predicates to) and
+                                each pass reads the labels once (Sec. 5
+                                grouping applied across queries); 2, one
+                                scan per plan */
     uint32_t frontier;       /* candidate sets those plans test later levels
                                 against: 0 or 1, bitmaps (the scan writes
                                 one candidate vector per variable; a test is

@@ -240,16 +240,20 @@ int union_slot(std::vector<uint32_t>& list, uint32_t p, bool add) {
 }
 
 // Does plan P fit into pass x (adding its predicates when it does)?
-bool pass_take(Pass& x, const ScanSpec& S) {
+// Slots the plan would add to pass x (SIZE_MAX when it does not fit).
+size_t pass_cost(Pass& x, const ScanSpec& S) {
     size_t new_out = 0, new_in = 0;
     for (int i = 0; i < S.n_out; ++i) new_out += union_slot(x.out_pred, S.out_pred[i], false) < 0;
     for (int i = 0; i < S.n_in; ++i) new_in += union_slot(x.in_pred, S.in_pred[i], false) < 0;
     if (x.out_pred.size() + new_out > (size_t)kMaxSlotsWide ||
         x.in_pred.size() + new_in > (size_t)kMaxSlotsWide)
-        return false;
+        return SIZE_MAX;
+    return new_out + new_in;
+}
+
+void pass_take(Pass& x, const ScanSpec& S) {
     for (int i = 0; i < S.n_out; ++i) union_slot(x.out_pred, S.out_pred[i], true);
     for (int i = 0; i < S.n_in; ++i) union_slot(x.in_pred, S.in_pred[i], true);
-    return true;
 }
 
 // A plan's slot mask renumbered from its own slots into the pass's.
@@ -333,8 +337,10 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
             ++n_in;
         }
     }
-    // plans that need a triple scan: packed into shared passes (in order,
-    // a new pass when the union would pass kMaxSlotsWide in a direction)
+    // plans that need a triple scan: packed into shared passes, each plan
+    // into the pass it adds the fewest new predicates to (the earliest on a
+    // tie; a plan whose predicates a pass already tests costs nothing), a
+    // new pass when none has room (kMaxSlotsWide per direction)
     std::vector<Pass> passes;
     std::vector<EvalVec> vecs;           // every pass's vectors, pass by pass
     std::vector<uint32_t> vec_off;       // first vector of each pass
@@ -344,12 +350,15 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
         for (uint32_t q = 0; q < n; ++q) {
             const gs_plan* P = plan_of(b, q);
             if (b->in_kernel[q] || !P->needs_scan) continue;
-            if (passes.empty() || !pass_take(passes.back(), P->scan)) {
-                passes.emplace_back();
-                pass_take(passes.back(), P->scan);
+            size_t best = SIZE_MAX, at = passes.size();
+            for (size_t k = 0; k < passes.size() && best > 0; ++k) {
+                const size_t c = pass_cost(passes[k], P->scan);
+                if (c < best) { best = c; at = k; }
             }
-            passes.back().queries.push_back(q);
-            b->pass_of[q] = (int32_t)passes.size() - 1;
+            if (at == passes.size()) passes.emplace_back();
+            pass_take(passes[at], P->scan);
+            passes[at].queries.push_back(q);
+            b->pass_of[q] = (int32_t)at;
         }
         const uint64_t words = (g->N + 31) / 32;
         for (Pass& x : passes) {

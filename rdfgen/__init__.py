@@ -483,17 +483,27 @@ def load_queries(path: str):
     return out
 
 
-BANDWIDTH_FILE = os.path.join(_HERE, "rmat26_bandwidth.txt")
+BANDWIDTH_QUERIES = 16
+
+
+def bandwidth_file(name: str = "rmat26") -> str:
+    """Where make_bandwidth_queries.py stores the family for a workload."""
+    return os.path.join(_HERE, "%s_bandwidth.txt" % name)
+
+
+BANDWIDTH_FILE = bandwidth_file("rmat26")
 
 
 def bandwidth_workload(w: Workload | None = None):
-    """The bandwidth-bound workload's queries as written by
-    make_bandwidth_queries.py (the same selection as bandwidth_queries on
-    the scale-26 graph, stored so that a run needs no sampler)."""
+    """The bandwidth-bound family's queries on w's graph (default: the
+    scale-26 workload) as written by make_bandwidth_queries.py (the
+    selection of bandwidth_queries, stored so that a run needs no
+    sampler)."""
     w = w or WORKLOADS["rmat26"]
-    qs = load_queries(BANDWIDTH_FILE)
-    if len(qs) != w.n_queries:
-        raise ValueError("%s holds %d queries, the workload %d" % (BANDWIDTH_FILE, len(qs), w.n_queries))
+    path = bandwidth_file(w.name)
+    qs = load_queries(path)
+    if len(qs) != BANDWIDTH_QUERIES:
+        raise ValueError("%s holds %d queries, the family %d" % (path, len(qs), BANDWIDTH_QUERIES))
     return qs
 
 

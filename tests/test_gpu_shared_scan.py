@@ -96,6 +96,14 @@ def test_wide_passes_beyond_16_predicates_per_direction():
         assert n_plans == len(pats)
         assert (2 <= n_scans < len(pats)) if frontier == 1 else n_scans == 1
         b.close()
+        # the same plans three times over: a repeat adds no predicate to the
+        # pass that holds its first occurrence, so it costs no further pass
+        rep = pats * 3
+        b = g.eval_batch([g.plan(q) for q in rep], config=gs.BatchConfig(frontier=frontier))
+        for i, q in enumerate(rep):
+            assert np.array_equal(b.fetch(i), ix.eval(q)), (frontier, i)
+        assert b.scans() == (n_scans, len(rep))
+        b.close()
     g.close()
 
 
