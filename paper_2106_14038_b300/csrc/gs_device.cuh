@@ -44,17 +44,39 @@ __device__ __forceinline__ void count_short(const uint32_t* __restrict__ a, uint
     }
 }
 
+// First position in [lo, hi) (hi - lo <= kShort) of the sorted a whose
+// value is >= key, by binary search: a handful of instructions per step,
+// for callers bound by instruction issue rather than by load latency.
+__device__ __forceinline__ uint32_t lower_bound_short(const uint32_t* __restrict__ a, uint32_t lo,
+                                                      uint32_t hi, uint32_t key) {
+    uint32_t n = hi - lo;
+    while (n > 0) {
+        const uint32_t half = n >> 1;
+        if (__ldg(a + lo + half) < key) {
+            lo += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return lo;
+}
+
 // First position in [lo, hi) of the sorted array a whose value is >= key
-// (hi when there is none).
+// (hi when there is none). kSearchShort: finish the last <= kShort entries
+// by binary search instead of counting them.
+template <bool kSearchShort = false>
 __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ a, uint32_t lo,
                                                     uint32_t hi, uint32_t key) {
     while (hi - lo > kShort) {
-        const uint32_t n = hi - lo;
+        // probes at lo + k * step, k = 1..8, step = floor(n / 9) >= 3: the
+        // last probe stays below hi and every part is at most step + 8 long
+        const uint32_t step = (hi - lo) / 9;
         uint32_t c = 0, last_lt = lo, first_ge = hi;
         uint32_t pos[8], val[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            pos[j] = lo + (uint32_t)(((uint64_t)n * (uint32_t)(j + 1)) / 9);
+            pos[j] = lo + step * (uint32_t)(j + 1);
             val[j] = __ldg(a + pos[j]);
         }
 #pragma unroll
@@ -66,6 +88,7 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__
         hi = first_ge;            // a[first_ge] >= key, so the answer is <= first_ge
         if (lo >= hi) return hi;
     }
+    if (kSearchShort) return lower_bound_short(a, lo, hi, key);
     uint32_t below, equal;
     count_short(a, lo, hi, key, below, equal);
     return lo + below;
@@ -122,16 +145,14 @@ __device__ __forceinline__ bool has_label(const DStore& S, uint32_t r, uint32_t 
     return l < e && ld(S.lab + l) == p;
 }
 
-// Is x in the sorted idx range [lo, lo + len)?
+// Is x in the sorted idx range [lo, lo + len)? (The candidate tests of the
+// level expansion make many of these; they are bound by instruction issue,
+// so short windows are searched rather than counted.)
 __device__ __forceinline__ bool in_range(const DStore& S, uint32_t lo, uint32_t len, uint32_t x) {
     if (len == 0) return false;
     const uint32_t hi = lo + len;
-    if (len <= kShort) {
-        uint32_t below, equal;
-        count_short(S.idx, lo, hi, x, below, equal);
-        return equal != 0;
-    }
-    const uint32_t k = lower_bound_u32(S.idx, lo, hi, x);
+    const uint32_t k = len <= kShort ? lower_bound_short(S.idx, lo, hi, x)
+                                     : lower_bound_u32<true>(S.idx, lo, hi, x);
     return k < hi && ld(S.idx + k) == x;
 }
 

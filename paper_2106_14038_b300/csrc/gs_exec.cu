@@ -134,7 +134,6 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
     chain_enter();
     Ctl* ctl = E.ctl;
     if (overflowed(ctl)) return;
-    __shared__ uint64_t tile_nodes[2];
     __shared__ uint64_t roff_s[kExpTileNodes];
     const uint64_t np = l == 0 ? 1 : ctl->n[l - 1];
     const uint32_t nbm = L.n_binders > 0 ? L.n_binders : 1;
@@ -148,12 +147,8 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
     const uint32_t* list = E.lists ? E.lists + (uint64_t)l * E.list_stride : nullptr;
     for (uint64_t t0 = (uint64_t)blockIdx.x * kExpTile; t0 < T; t0 += (uint64_t)gridDim.x * kExpTile) {
         uint64_t t1 = min(t0 + kExpTile, T);
-        if (threadIdx.x == 0) {
-            tile_nodes[0] = upper_bound_roff(S.roff, ctl, ch, 0, np, t0) - 1;
-            tile_nodes[1] = upper_bound_roff(S.roff, ctl, ch, tile_nodes[0], np, t1 - 1);
-        }
-        __syncthreads();
-        const uint64_t i0 = tile_nodes[0], i1 = tile_nodes[1];
+        const uint64_t i0 = block_upper_bound_roff(S.roff, ctl, ch, 0, np, t0) - 1;
+        const uint64_t i1 = block_upper_bound_roff(S.roff, ctl, ch, i0, np, t1 - 1);
         // the tile's node offsets in shared memory (when they fit): the
         // candidate -> node search then runs there
         const bool local = i1 - i0 <= kExpTileNodes;
@@ -315,7 +310,6 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
     Ctl* ctl = E.ctl;
     if (overflowed(ctl) || (ctl->status & kStHuge)) return;
     __shared__ const uint2* lv[kMaxLevels];
-    __shared__ uint64_t tile_nodes[2];
     __shared__ __align__(16) uint32_t stage[kEnumStageWords];
     __shared__ uint64_t roff_s[kEnumTileNodes + 1];
     load_levels(E, last, lv);
@@ -338,12 +332,8 @@ __global__ void __launch_bounds__(kThreads) k_enum_write(ExecDev E, int last, En
     const uint32_t tile_rows = min(kThreads * 8u, (kEnumStageWords / nv) & ~3u);
     for (uint64_t t0 = (uint64_t)blockIdx.x * tile_rows; t0 < T; t0 += (uint64_t)gridDim.x * tile_rows) {
         const uint64_t t1 = min(t0 + tile_rows, T);
-        if (threadIdx.x == 0) {
-            tile_nodes[0] = upper_bound_roff(S.roff, ctl, ch, 0, n, t0) - 1;
-            tile_nodes[1] = upper_bound_roff(S.roff, ctl, ch, tile_nodes[0], n, t1 - 1);
-        }
-        __syncthreads();
-        const uint64_t i0 = tile_nodes[0], i1 = tile_nodes[1];
+        const uint64_t i0 = block_upper_bound_roff(S.roff, ctl, ch, 0, n, t0) - 1;
+        const uint64_t i1 = block_upper_bound_roff(S.roff, ctl, ch, i0, n, t1 - 1);
         // the tile's node offsets in shared memory (when they fit): the row ->
         // node search then runs there
         const bool local = i1 - i0 <= kEnumTileNodes;

@@ -206,6 +206,29 @@ __device__ __forceinline__ uint32_t root_word_mask(const ExecDev& E, uint32_t w)
     return m;
 }
 
+// upper_bound_roff computed by the whole block (every thread calls it with
+// the same arguments and gets the answer): each round probes kThreads
+// evenly spaced items at once and counts those <= key (the offsets are
+// non-decreasing, so the true probes are a prefix), shrinking the interval
+// kThreads-fold; a tile's node bounds then take a few barriers instead of
+// one thread's chain of dependent loads while the block waits.
+__device__ __forceinline__ uint64_t block_upper_bound_roff(const uint64_t* roff, const Ctl* ctl,
+                                                           uint32_t chunk, uint64_t lo, uint64_t hi,
+                                                           uint64_t key) {
+    while (lo < hi) {
+        const uint64_t n = hi - lo;
+        const uint64_t step = (n + kThreads - 1) / kThreads;
+        const uint64_t p = lo + (uint64_t)threadIdx.x * step;
+        const int c = __syncthreads_count(p < hi && roff_at(roff, ctl, chunk, p) <= key);
+        if (c == 0) return lo;
+        if (step == 1) return lo + (uint64_t)c;
+        const uint64_t nlo = lo + (uint64_t)(c - 1) * step + 1;
+        hi = min(hi, lo + (uint64_t)c * step);
+        lo = nlo;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ bool self_ok(const ExecDev& E, const LevelSpec& L, uint32_t x) {
     for (int j = 0; j < L.n_self; ++j) {
         uint32_t lo, len;
