@@ -188,6 +188,36 @@ __device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t v, uint64_t* to
     return base + incl - v;
 }
 
+// Exclusive max-scan of one value per thread over a block of kThreads
+// threads (0 for thread 0).
+__device__ __forceinline__ uint32_t block_excl_max_u32(uint32_t v) {
+    __shared__ uint32_t wmax[kThreads / 32];
+    const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= (uint32_t)d) incl = max(incl, t);
+    }
+    if (lane == 31) wmax[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t x = lane < kThreads / 32 ? wmax[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= (uint32_t)d) x = max(x, t);
+        }
+        if (lane < kThreads / 32) wmax[lane] = x;
+    }
+    __syncthreads();
+    uint32_t ex = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) ex = 0;
+    if (w > 0) ex = max(ex, wmax[w - 1]);
+    __syncthreads();
+    return ex;
+}
+
 __device__ __forceinline__ uint64_t block_sum_u64(uint64_t v) {
     uint64_t t;
     block_excl_scan_u64(v, &t);

@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
     Ctl* ctl = E.ctl;
     if (overflowed(ctl)) return;
     __shared__ uint64_t roff_s[kExpTileNodes];
+    __shared__ uint32_t owner[kExpTile];
     const uint64_t np = l == 0 ? 1 : ctl->n[l - 1];
     const uint32_t nbm = L.n_binders > 0 ? L.n_binders : 1;
     Scratch S = scratch_at(E, np, nbm);
@@ -149,12 +150,32 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
         uint64_t t1 = min(t0 + kExpTile, T);
         const uint64_t i0 = block_upper_bound_roff(S.roff, ctl, ch, 0, np, t0) - 1;
         const uint64_t i1 = block_upper_bound_roff(S.roff, ctl, ch, i0, np, t1 - 1);
-        // the tile's node offsets in shared memory (when they fit): the
-        // candidate -> node search then runs there
+        // When the tile's nodes fit in shared memory, its candidates find
+        // their nodes there without a search: owner[u] is marked with the
+        // last node k whose first candidate is t0 + u (nodes without
+        // candidates share the next node's offset, and the last of them is
+        // the one that has some), and a max-scan over the tile carries each
+        // mark forward to the candidates that follow it.
         const bool local = i1 - i0 <= kExpTileNodes;
-        if (local)
-            for (uint64_t k = threadIdx.x; k < i1 - i0; k += kThreads)
-                roff_s[k] = roff_at(S.roff, ctl, ch, i0 + k);
+        if (local) {
+            for (uint32_t u = threadIdx.x; u < kExpTile; u += kThreads) owner[u] = 0;
+            __syncthreads();
+            for (uint64_t k = threadIdx.x; k < i1 - i0; k += kThreads) {
+                const uint64_t o = roff_at(S.roff, ctl, ch, i0 + k);
+                roff_s[k] = o;
+                if (o >= t0 && o < t1) atomicMax(&owner[o - t0], (uint32_t)k);
+            }
+            __syncthreads();
+            uint32_t run = 0, m[kExpItems];
+#pragma unroll
+            for (int e = 0; e < kExpItems; ++e) {
+                run = max(run, owner[threadIdx.x * kExpItems + e]);
+                m[e] = run;
+            }
+            const uint32_t before = block_excl_max_u32(run);
+#pragma unroll
+            for (int e = 0; e < kExpItems; ++e) owner[threadIdx.x * kExpItems + e] = max(m[e], before);
+        }
         __syncthreads();
         for (int k = 0; k < kExpItems; ++k) {
             uint64_t q = t0 + (uint64_t)k * kThreads + threadIdx.x;
@@ -163,13 +184,9 @@ __global__ void __launch_bounds__(kThreads) k_expand(ExecDev E, int l, LevelSpec
             if (q < t1) {
                 uint64_t i, j;
                 if (local) {
-                    uint32_t lo = 0, hi = (uint32_t)(i1 - i0);   // last k with roff_s[k] <= q
-                    while (hi - lo > 1) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (roff_s[mid] <= q) lo = mid; else hi = mid;
-                    }
-                    i = i0 + lo;
-                    j = q - roff_s[lo];
+                    const uint32_t k = owner[q - t0];
+                    i = i0 + k;
+                    j = q - roff_s[k];
                 } else {
                     i = upper_bound_roff(S.roff, ctl, ch, i0, i1, q) - 1;
                     j = q - roff_at(S.roff, ctl, ch, i);
