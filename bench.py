@@ -444,8 +444,8 @@ def run_gsmart(args):
 # sha1 prefix of the scan source the counters were taken on; the summary is
 # in profiles/. A changed kernel reports null until it is captured again.
 SCAN_TRAFFIC = {
-    "rmat22": ("52b3e7feb70b", 617061632),
-    "rmat26": ("52b3e7feb70b", 10649042944),
+    "rmat22": ("f675e7461d73", 617415936),
+    "rmat26": ("f675e7461d73", 10649202944),
 }
 
 
