@@ -5,10 +5,11 @@ Query q has the shape and constants rdfgen gives it (2..10 shape vertices,
 star / chain / cycle / snowflake, 1..2 constants) and a target count t drawn
 log-uniformly from [1, 10^6]. Its seeded embeddings are tried in order; the
 first whose exact answer count (the oracle's count mode) lies in [t/2, 2t]
-is kept, else, after 64 tries, the one whose count is nearest t on a log
-scale. Counts that take the oracle more than 2e7 join steps are not used;
-a query none of whose tries finishes within that is left out (the header
-says how many). Every query kept has at least its embedding as an answer.
+is kept, else, after 24 tries, the one whose count is nearest t on a log
+scale. A count may take the oracle at most 10^5 + 50 t join steps (a count
+in [t/2, 2t] needs far fewer); tries past that are not used, and a query
+none of whose tries finishes is left out (the header says how many). Every
+query kept has at least its embedding as an answer.
 
     python tests/golden/make_rmat24_batched.py
 """
@@ -25,8 +26,11 @@ import oracle  # noqa: E402
 import rdfgen  # noqa: E402
 
 OUT = os.path.join(ROOT, "tests", "golden", "rmat24_batched.txt")
-TRIES = 64
-MAX_STEPS = 20_000_000
+TRIES = 24
+
+
+def max_steps(t: float) -> int:
+    return int(1e5 + 50 * t)
 
 
 def main():
@@ -44,7 +48,7 @@ def main():
             emb = sm.embed(sh, w.query_seed, q * 100003 + a, with_bound=False)
             if emb is None:
                 continue
-            n, _, done = ix.count(emb.patterns, threads=1, max_steps=MAX_STEPS)
+            n, _, done = ix.count(emb.patterns, threads=1, max_steps=max_steps(t))
             if not done:
                 continue
             d = abs(math.log(max(n, 1)) - math.log(t))
@@ -58,8 +62,12 @@ def main():
         emb.bound = float(n)          # the exact count
         return emb, t
 
+    got = []
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-        got = list(ex.map(one, range(len(pairs))))
+        for i, r in enumerate(ex.map(one, range(len(pairs)))):
+            got.append(r)
+            if (i + 1) % 256 == 0:
+                print("%d of %d queries in %.0f s" % (i + 1, len(pairs), time.time() - t0), flush=True)
     dropped = sum(1 for g in got if g is None)
     got = [g for g in got if g is not None]
     qs = [e for e, _ in got]
@@ -69,11 +77,11 @@ def main():
               "Written by tests/golden/make_rmat24_batched.py in %.0f s: per query the first "
               "embedding whose exact answer count (oracle count mode) lies in [t/2, 2t], t "
               "log-uniform in [1, 1e6]; %d of %d within, the others nearest t; %d left out "
-              "(no try counted within %d join steps).\n"
+              "(no try counted within 1e5 + 50 t join steps).\n"
               "Per line: shape, exact answer count, patterns, then s p o per pattern "
               "(variable k is -(k+1))."
               % (len(qs), w.scale, w.n_edges.bit_length() - 1, w.n_preds, w.zipf_s, w.graph_seed,
-                 w.query_seed, time.time() - t0, inside, len(qs), dropped, MAX_STEPS))
+                 w.query_seed, time.time() - t0, inside, len(qs), dropped))
     rdfgen.save_queries(OUT, qs, header)
     print("wrote %s (%d of %d within [t/2, 2t])" % (OUT, inside, len(qs)))
 
