@@ -611,6 +611,11 @@ def run_batched(args):
     plain_ms = 1000 * (time.perf_counter() - t1)
     total_rows = int(np.sum(rows))
     assert prow == total_rows, (prow, total_rows)
+    # with the stored selection, every query's row count is its oracle count
+    counts_match = None
+    if selection.startswith("exact"):
+        counts_match = bool(np.array_equal(np.asarray(rows, np.int64),
+                                           np.array([int(q.bound) for q in qs], np.int64)))
     t_ms = float(np.mean(b_ms))
     bounds = np.array([q.bound for q in qs])
     print(json.dumps({
@@ -623,6 +628,7 @@ def run_batched(args):
                    "predicates": w.n_preds, "queries": len(qs),
                    "selection": selection,
                    "count_quantiles": [float(x) for x in np.quantile(bounds, [0, .1, .5, .9, 1])],
+                   "counts_match_oracle": counts_match,
                    "l2": "flushed before every step (256 MiB write)",
                    "setup_s": prep_s},
         "batched": {"config": bcfg.as_dict(), "autotune_best_ms_on_512": tune_ms,
