@@ -464,7 +464,8 @@ def save_queries(path: str, qs, header: str = ""):
         for line in header.splitlines():
             f.write("# %s\n" % line)
         for q in qs:
-            f.write("%s %.6g %d %s\n" % (q.shape, q.bound, len(q.patterns),
+            # %.17g keeps an exact count (any integer below 2^53) exact
+            f.write("%s %.17g %d %s\n" % (q.shape, q.bound, len(q.patterns),
                                          " ".join(str(int(x)) for x in q.patterns.reshape(-1))))
 
 
