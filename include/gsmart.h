@@ -220,6 +220,22 @@ gs_status gs_fetch_bindings(gs_result* r, int32_t* dst, uint64_t cap_rows, int d
  * ran in the single-CTA kernel (its levels are not kept). */
 gs_status gs_result_tree(gs_result* r, uint64_t* nodes, uint32_t cap, uint32_t* n_levels);
 
+/* Tracing (the phase breakdown of Sec. 9.1.2, on the device). With
+ * gs_graph_set_trace(g, 1), every grid-path evaluation on g records CUDA
+ * events between its phases: setup and triple scan, then each level of
+ * the binding tree (Sec. 7.1), then the enumeration of the answers.
+ * gs_result_phases writes their device milliseconds into ms[0 ..
+ * *n_phases) in that order (*n_phases = levels + 2; waits like
+ * gs_result_info). The events may keep consecutive kernels from
+ * overlapping, so traced times can exceed untraced ones. GS_ENOTIMPL when
+ * the result has no phase events (tracing was off when it was enqueued, or
+ * it ran in the single-CTA kernel); GS_EOVERFLOW (with *n_phases set) when
+ * cap < *n_phases. Host entry points also mark NVTX ranges (store build,
+ * planning, evaluation enqueue and waits, answer fetches, batch launches,
+ * server admissions), visible to a profiler that records them. */
+gs_status gs_graph_set_trace(gs_graph* g, int on);
+gs_status gs_result_phases(gs_result* r, float* ms, uint32_t cap, uint32_t* n_phases);
+
 /* Statistics of the last evaluation of r (synchronizes): device time in
  * milliseconds from CUDA events around the enqueued work, and the number of
  * kernels it launched. For a query the single CTA handed back, both cover

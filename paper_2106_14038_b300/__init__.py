@@ -39,7 +39,8 @@ EXPORTED = ["gs_load_triples", "gs_graph_info", "gs_graph_export", "gs_plan_quer
             "gs_plan_estimate", "gs_server_ticket", "gs_server_admission",
             "gs_server_submit_many", "gs_lspm_build", "gs_lspm_for_plan", "gs_lspm_info",
             "gs_lspm_export", "gs_eval_query_lspm", "gs_free_lspm", "gs_server_work",
-            "gs_result_tree", "gs_plan_paths", "gs_eval_query_roots", "gs_plan_root"]
+            "gs_result_tree", "gs_plan_paths", "gs_eval_query_roots", "gs_plan_root",
+            "gs_graph_set_trace", "gs_result_phases"]
 
 
 class GsError(RuntimeError):
@@ -137,6 +138,8 @@ def load_library(path: str | None = None):
         "gs_eval_query": [vp, vp, vp, P(vp)],
         "gs_eval_query_roots": [vp, vp, u32, u32, vp, P(vp)],
         "gs_plan_root": [vp, P(u32)],
+        "gs_graph_set_trace": [vp, i32],
+        "gs_result_phases": [vp, vp, u32, P(u32)],
         "gs_result_info": [vp, P(u64), P(u32)],
         "gs_fetch_bindings": [vp, vp, u64, i32, i32],
         "gs_result_stats": [vp, P(ctypes.c_float), P(u32)],
@@ -262,6 +265,11 @@ class Graph:
                                     idx.ctypes.data_as(ctypes.c_void_p),
                                     lab.ctypes.data_as(ctypes.c_void_p), 0, _stream_handle(stream)))
         return ptr, idx[:self.n_triples], lab[:self.n_triples]
+
+    def set_trace(self, on: bool = True):
+        """Record per-phase CUDA events in later grid-path evaluations
+        (Result.phases)."""
+        _check(_lib.gs_graph_set_trace(self._h, int(bool(on))))
 
     def plan(self, patterns, flags: int = PLAN_DEGREE) -> "Plan":
         return Plan(self, patterns, flags)
@@ -698,6 +706,15 @@ class Result:
         buf = np.zeros(32, np.uint64)
         n = ctypes.c_uint32()
         _check(_lib.gs_result_tree(self._h, buf.ctypes.data_as(ctypes.c_void_p), 32, ctypes.byref(n)))
+        return buf[:n.value].tolist()
+
+    def phases(self):
+        """Device ms of the traced phases: [setup + triple scan, level 0,
+        ..., level L-1, enumeration] (needs Graph.set_trace(True) before
+        the evaluation, and the grid path)."""
+        buf = np.zeros(40, np.float32)
+        n = ctypes.c_uint32()
+        _check(_lib.gs_result_phases(self._h, buf.ctypes.data_as(ctypes.c_void_p), 40, ctypes.byref(n)))
         return buf[:n.value].tolist()
 
     def time_ms(self) -> float:

@@ -87,6 +87,7 @@ struct gs_result {
     bool root_cut = false;        // only roots in [root_lo, root_hi) (gs_eval_query_roots)
     uint32_t root_lo = 0, root_hi = 0;
     std::vector<uint64_t> path_nodes;   // per-path mode: binding-tree nodes of each path
+    std::vector<cudaEvent_t> phase_ev;  // traced grid-path evaluation: after setup + scan, each level, enumeration
     uint32_t launches = 0;
     uint64_t rows = 0;
     uint64_t out_off = 0;
@@ -162,12 +163,23 @@ ExecDev exec_view(gs_result* r) {
 }
 
 gs_status enqueue(gs_result* r) {
+    NvtxRange nv("gs_eval: enqueue");
     if (r->scan_ready) GS_CUDA(cudaStreamWaitEvent(r->st, r->scan_ready, 0));
+    const cudaEvent_t* phases = nullptr;
+    if (r->mode == 0 && r->g->trace.load()) {
+        const size_t n = (size_t)r->plan.n_levels + 2;
+        while (r->phase_ev.size() < n) {
+            cudaEvent_t e = nullptr;
+            GS_CUDA(cudaEventCreate(&e));
+            r->phase_ev.push_back(e);
+        }
+        phases = r->phase_ev.data();
+    }
     GS_CUDA(cudaEventRecord(r->ev0, r->st));
     gs_status rc = r->mode == 1
         ? enqueue_small(&r->plan, exec_view(r), &r->launches, r->st)
         : enqueue_eval(r->g, &r->plan, exec_view(r), r->work, &r->launches, r->st, r->resume,
-                       r->scan_status, r->so, r->si);
+                       r->scan_status, r->so, r->si, phases);
     if (rc != GS_OK) return rc;
     GS_CUDA(cudaEventRecord(r->ev1, r->st));
     // the head of the control block follows the kernels to pinned memory
@@ -179,6 +191,7 @@ gs_status enqueue(gs_result* r) {
 
 gs_status wait_result(gs_result* r) {
     if (r->ready) return GS_OK;
+    NvtxRange nv("gs_eval: wait");
     for (int attempt = 0; attempt < kMaxRetries; ++attempt) {
         GS_CUDA(cudaEventSynchronize(r->ev2));
         Ctl head;
@@ -251,6 +264,7 @@ void release(gs_result* r) {
     }
     const cudaEvent_t ev[3] = {r->ev0, r->ev1, r->ev2};
     if (r->g) give_host_res(r->g, ev, r->head);
+    for (cudaEvent_t e : r->phase_ev) cudaEventDestroy(e);
     delete r;
 }
 
@@ -274,6 +288,7 @@ gs_status gs_load_triples(const uint32_t* s, const uint32_t* p, const uint32_t* 
                           const gs_allocator* alloc, void* cuda_stream, gs_graph** out) {
     if (!out) { set_error("gs_load_triples: out is NULL"); return GS_EINVAL; }
     *out = nullptr;
+    NvtxRange nv("gs_load_triples");
     if (n && (!s || !p || !o)) { set_error("gs_load_triples: NULL triple array"); return GS_EINVAL; }
     if (n_vertices == 0 || n_vertices > (1u << 31)) { set_error("gs_load_triples: n_vertices must be in 1..2^31"); return GS_EINVAL; }
     if (n_predicates == 0 || n_predicates > 65535) { set_error("gs_load_triples: n_predicates must be in 1..65535"); return GS_EINVAL; }
@@ -350,6 +365,7 @@ gs_status gs_graph_export(const gs_graph* g, int by_column, uint32_t* ptr, uint3
 gs_status gs_plan_query(const gs_graph* g, const int64_t* patterns, uint32_t n_patterns,
                         uint32_t flags, gs_plan** out) {
     if (!out) { set_error("gs_plan_query: out is NULL"); return GS_EINVAL; }
+    NvtxRange nv("gs_plan_query");
     return make_plan(g, patterns, n_patterns, flags, out);
 }
 
@@ -794,6 +810,35 @@ gs_status gs_result_tree(gs_result* r, uint64_t* nodes, uint32_t cap, uint32_t* 
     return GS_OK;
 }
 
+gs_status gs_graph_set_trace(gs_graph* g, int on) {
+    if (!g) { set_error("gs_graph_set_trace: graph is NULL"); return GS_EINVAL; }
+    g->trace.store(on ? 1 : 0);
+    return GS_OK;
+}
+
+gs_status gs_result_phases(gs_result* r, float* ms, uint32_t cap, uint32_t* n_phases) {
+    if (!r || !n_phases) { set_error("gs_result_phases: NULL argument"); return GS_EINVAL; }
+    gs_status rc = wait_result(r);
+    if (rc != GS_OK) return rc;
+    const uint32_t n = (uint32_t)r->plan.n_levels + 2;
+    if (r->mode != 0 || r->phase_ev.size() < n) {
+        set_error("gs_result_phases: no phase events (tracing was off, or the query ran in the single-CTA kernel)");
+        return GS_ENOTIMPL;
+    }
+    *n_phases = n;
+    if (cap < n) {
+        set_error("gs_result_phases: room for %u phases, the evaluation has %u", cap, n);
+        return GS_EOVERFLOW;
+    }
+    if (!ms) { set_error("gs_result_phases: ms is NULL"); return GS_EINVAL; }
+    cudaEvent_t prev = r->ev0;
+    for (uint32_t i = 0; i < n; ++i) {
+        GS_CUDA(cudaEventElapsedTime(ms + i, prev, r->phase_ev[i]));
+        prev = r->phase_ev[i];
+    }
+    return GS_OK;
+}
+
 gs_status gs_result_stats(gs_result* r, float* device_ms, uint32_t* kernel_launches) {
     if (!r) { set_error("gs_result_stats: result is NULL"); return GS_EINVAL; }
     gs_status rc = wait_result(r);
@@ -806,6 +851,7 @@ gs_status gs_result_stats(gs_result* r, float* device_ms, uint32_t* kernel_launc
 gs_status gs_fetch_bindings(gs_result* r, int32_t* dst, uint64_t cap_rows, int dst_on_device,
                             int sort_rows) {
     if (!r) { set_error("gs_fetch_bindings: result is NULL"); return GS_EINVAL; }
+    NvtxRange nv("gs_fetch_bindings");
     gs_status rc = wait_result(r);
     if (rc != GS_OK) return rc;
     if (cap_rows < r->rows) {

@@ -284,6 +284,7 @@ gs_status gs::eval_batch_ex(gs_graph* g, const gs_plan* const* plans, uint32_t n
                             const gs_batch_config* cfg, int max_blocks, gs_batch** out) {
     if (!g || !out || (n && !plans)) { set_error("gs_eval_batch: NULL argument"); return GS_EINVAL; }
     *out = nullptr;
+    NvtxRange nv("gs_eval_batch: pack and launch");
     for (uint32_t q = 0; q < n; ++q) {
         if (!plans[q]) { set_error("gs_eval_batch: plan %u is NULL", q); return GS_EINVAL; }
         if (plans[q]->N != 0 && (plans[q]->N != g->N || plans[q]->P != g->P)) {

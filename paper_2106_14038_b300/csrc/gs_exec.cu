@@ -431,7 +431,7 @@ uint64_t host_level_off(const uint64_t* n, int l) {
 
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
                        cudaStream_t st, int start_level, const uint32_t* scanned, const Store* so,
-                       const Store* si) {
+                       const Store* si, const cudaEvent_t* phase_ev) {
     const dim3 nb(g->n_blocks), th(kThreads);
     Ctl* ctl = E.ctl;
     uint32_t nl_launch = 1;
@@ -453,17 +453,25 @@ gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, vo
             nl_launch += 3;
         }
     }
+    if (phase_ev) {
+        for (int l = 0; l <= start_level && l <= P->n_levels; ++l)   // setup and scan; levels resumed past
+            GS_CUDA(cudaEventRecord(phase_ev[l], st));
+    }
     for (int l = start_level; l < P->n_levels; ++l) {
         const LevelSpec& L = P->levels[l];
         if (L.src == kSrcList) {
             GS_CUDA(launch_chained(k_bits_count, nb, th, 0, st, E, l, L));
             GS_CUDA(launch_chained(k_bits_write, nb, th, 0, st, E, l, L, l == 0 ? 1 : 0));
             nl_launch += 2;
-            if (l == 0) continue;
+            if (l == 0) {
+                if (phase_ev) GS_CUDA(cudaEventRecord(phase_ev[1], st));
+                continue;
+            }
         }
         GS_CUDA(launch_chained(k_range, dim3(g->range_blocks), th, 0, st, E, l, L));
         GS_CUDA(launch_chained(k_expand, dim3(g->expand_blocks), th, 0, st, E, l, L));
         nl_launch += 2;
+        if (phase_ev) GS_CUDA(cudaEventRecord(phase_ev[l + 1], st));
     }
     const int last = P->n_levels - 1;
     EnumSpec F{};
@@ -476,6 +484,7 @@ gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, vo
     GS_CUDA(launch_chained(k_enum_range, nb, th, 0, st, E, last, F));
     GS_CUDA(launch_chained(k_enum_write, nb, th, 0, st, E, last, F));
     nl_launch += 2;
+    if (phase_ev) GS_CUDA(cudaEventRecord(phase_ev[P->n_levels + 1], st));
     if (launches) *launches = nl_launch;
     GS_CUDA(cudaGetLastError());
     return GS_OK;

@@ -158,9 +158,12 @@ gs_status enqueue_small(const gs_plan* P, const ExecDev& E, uint32_t* launches, 
 // workspace (a plan without triple scan). scanned != NULL: the candidate
 // vectors are already in E.bits (a triple scan shared with other queries,
 // whose status word `scanned` is); the query runs no scan of its own.
+// phase_ev (NULL: none): P->n_levels + 2 events recorded after the setup
+// and triple scan, after each level, and after the enumeration.
 gs_status enqueue_eval(const gs_graph* g, const gs_plan* P, const ExecDev& E, void* scan_work, uint32_t* launches,
                        cudaStream_t st, int start_level = 0, const uint32_t* scanned = nullptr,
-                       const Store* so = nullptr, const Store* si = nullptr);
+                       const Store* so = nullptr, const Store* si = nullptr,
+                       const cudaEvent_t* phase_ev = nullptr);
 // As eval_query_prescanned, but bits stay the caller's (several results
 // read one set of candidate vectors).
 gs_status eval_query_borrowed(gs_graph* g, const gs_plan* plan, void* cuda_stream, uint32_t* bits,

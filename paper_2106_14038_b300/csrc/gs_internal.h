@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gsmart.h"
 
 namespace gs {
@@ -82,6 +84,16 @@ struct Alloc {
 // of idx (the other end) and lab (the predicate), sorted by (lab, idx).
 // ptr, idx and lab are padded with 4 zero words so aligned 16-byte loads
 // and bulk copies that start inside the array stay inside the allocation.
+// A named NVTX range over a host-side step (a no-op unless a profiler is
+// attached): the store build, planning, evaluation enqueue, waits, batch
+// and server admission.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct Store {
     uint32_t* ptr = nullptr;
     uint32_t* idx = nullptr;
@@ -136,6 +148,7 @@ struct gs_graph {
     cudaStream_t side[16] = {};
     int n_side = 0;
     std::atomic<uint32_t> side_rr{0};   // where the next batch starts on the side streams
+    std::atomic<int> trace{0};          // grid-path evaluations record per-phase events
     // host copies of the row lengths (out = CSR, in = CSC), used to route
     // queries whose first level is certainly large away from the
     // single-CTA evaluator

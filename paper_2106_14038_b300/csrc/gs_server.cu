@@ -186,6 +186,7 @@ void worker_loop(gs_server* s) {
                 // waited 50 x max_wait_us: then nothing passes it and memory
                 // drains until it fits. A ticket that cannot fit even alone
                 // is admitted alone once nothing else is in flight.
+                NvtxRange nv("gs_server: admit a batch");
                 Admit a;
                 std::vector<uint64_t> take_ids;
                 uint64_t bytes = 0;

@@ -238,3 +238,10 @@ def test_plan_root_and_root_range_arguments():
     h = ctypes.c_void_p(1)
     assert lib.gs_eval_query_roots(None, p._h, 0, 10, None, ctypes.byref(h)) == 1
     assert h.value is None                                         # *out cleared on error
+
+
+def test_trace_arguments():
+    lib = gs.load_library()
+    assert lib.gs_graph_set_trace(None, 1) == 1                      # GS_EINVAL
+    n = ctypes.c_uint32()
+    assert lib.gs_result_phases(None, None, 0, ctypes.byref(n)) == 1
