@@ -60,6 +60,9 @@ def _args():
     ap.add_argument("--family", default="default", choices=["default", "bandwidth"],
                     help="query mode: the workload's own queries, or the bandwidth family's "
                          "copy for its graph (rdfgen/<workload>_bandwidth.txt)")
+    ap.add_argument("--trace", action="store_true",
+                    help="query mode: also report each query's device ms per phase "
+                         "(setup + triple scan, each level, enumeration; grid-path queries)")
     ap.add_argument("--batch", action="store_true",
                     help="query mode: evaluate the selected queries as one batch per round")
     return ap.parse_args()
@@ -733,7 +736,10 @@ def run_query(args):
         return
     dev = {i: [] for i in sel}
     info = {}
+    phases = {i: [] for i in sel}
     launches = 0
+    if args.trace:
+        g.set_trace(True)
     for rep in range(args.warmup + args.steps):
         for i in sel:
             plan = g.plan(qs[i].patterns)
@@ -743,6 +749,11 @@ def run_query(args):
             if rep >= args.warmup:
                 dev[i].append(ms)
                 launches += nl
+                if args.trace:
+                    try:
+                        phases[i].append(r.phases())
+                    except gs.GsError:
+                        pass
             if rep == 0:
                 try:
                     tree = r.tree()
@@ -757,7 +768,9 @@ def run_query(args):
         "config": {"workload": w.name, "family": args.family, "queries": sel},
         "queries": [{"index": i, "shape": info[i][0], "rows": info[i][1], "launches": info[i][2],
                      "tree_nodes": info[i][3], "estimate_bytes": info[i][4][0],
-                     "estimate_rows": info[i][4][1], "device_ms": float(np.mean(dev[i]))}
+                     "estimate_rows": info[i][4][1], "device_ms": float(np.mean(dev[i])),
+                     "phases_ms": ([float(x) for x in np.mean(np.array(phases[i]), axis=0)]
+                                   if phases[i] else None)}
                     for i in sel],
         "gpu_launches": launches,
     }), flush=True)
