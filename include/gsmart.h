@@ -48,7 +48,7 @@ typedef enum {
     GS_ECUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error) */
     GS_EOVERFLOW = 4,  /* a caller buffer is too small (nothing written) */
     GS_ETIMEOUT = 5,   /* a bounded device-side wait ran out */
-    GS_ENOTIMPL = 6    /* feature not available in this build */
+    GS_ENOTIMPL = 6    /* not supported for these arguments (the call says which) */
 } gs_status;
 
 /* Device allocation hook. alloc returns NULL on failure, else memory
