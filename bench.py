@@ -536,7 +536,8 @@ def run_scan_only(args):
         "roofline": {"kernel": "triple-scan call (k_scan_zero + k_scan over both orientations "
                                "+ k_scan_eval)", "bound": "hbm", "achieved": gbs,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
-                     "peak_source": which, "traffic": _scan_traffic(w.name),
+                     "peak_source": which, "peak_nominal": NOMINAL_HBM_GBS,
+                     "frac_nominal": gbs / NOMINAL_HBM_GBS, "traffic": _scan_traffic(w.name),
                      "algorithmic_bytes": alg},
         "clocks": clk.summary(), "gpu_launches": 3 * args.steps,
     }), flush=True)
@@ -946,6 +947,9 @@ def _served_entry(srv, rate, n, sched, lat_us, done_s):
             "peak_admitted_bytes": peak}
 
 
+NOMINAL_HBM_GBS = 7700.0   # the B300's nominal HBM3e bandwidth, reported beside the measured peak
+
+
 def _scan_roofline(g, w, stream, peaks, which, n_scan=20):
     """The triple-scan call (Eq. 17 / Eq. 21 over the whole matrix) timed
     alone with CUDA events: algorithmic bytes 2 (4 (N + 1) + 4 M) + N / 8."""
@@ -975,6 +979,7 @@ def _scan_roofline(g, w, stream, peaks, which, n_scan=20):
                       "orientations + k_scan_eval)",
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "peak_source": which,
+            "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
             "traffic": _scan_traffic(w.name), "algorithmic_bytes": alg, "ms_per_launch": scan_ms,
             "ms_median": float(np.median(ms))}
 
