@@ -299,8 +299,9 @@ gs_status gs_eval_batch_cfg(gs_graph* g, const gs_plan* const* plans, uint32_t n
 
 /* Autotuner: evaluates the n plans (a sample of the workload) under a fixed
  * set of candidate configurations, each twice, and returns in *best the one
- * with the smallest wall time from enqueue to the last answer count, which
- * goes to *best_ms (may be NULL). Stage 1 tries CTAs per SM x candidate
+ * with the smallest wall time from enqueue to the last answer count (of
+ * those within 3% of it, the one that hands the fewest queries to the grid
+ * path), whose time goes to *best_ms (may be NULL). Stage 1 tries CTAs per SM x candidate
  * budget x row budget; stage 2, when the sample holds plans with a triple
  * scan, tries shared or per-plan scans x bitmap or list frontier x 4 or 16
  * grid-path streams under the stage-1 choice. The choice is kept for the life of the process, keyed by
@@ -342,7 +343,8 @@ void gs_free_batch(gs_batch* b);
 /* Serving loop (continuous batching). The server keeps the graph resident
  * and owns a worker thread and a pool of CUDA streams. Submitted plans wait
  * in arrival order; when the device is idle, when max_batch / 8 plans
- * wait, or when the oldest has waited max_wait_us, the worker admits
+ * wait, or when the oldest has waited max_wait_us or half the running mean
+ * time of the server's batches (whichever is longer), the worker admits
  * waiting plans into a batch (as in gs_eval_batch) while a stream is free
  * and the batch's estimated device bytes fit the memory budget together
  * with the batches in flight. A plan's bytes are its estimated
@@ -364,9 +366,11 @@ typedef struct {
     uint32_t max_batch;              /* queries per batch (0: 1024) */
     uint32_t n_streams;              /* batches in flight (0: 4) */
     uint64_t memory_budget;          /* bytes of device memory (0: 40 GiB) */
-    uint32_t max_wait_us;            /* while batches run, the longest a
+    uint32_t max_wait_us;            /* while batches run, the least time a
                                         queued query waits for more arrivals
-                                        before it starts a batch (0: 200) */
+                                        before it starts a batch (0: 200;
+                                        half the mean batch time when that
+                                        is longer) */
     uint64_t pool_bytes_per_query;   /* largest answer-pool share of one
                                         query (0: 16 MiB) */
     gs_batch_config batch;           /* tunables of every batch (zero fields:

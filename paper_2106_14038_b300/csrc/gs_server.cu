@@ -41,6 +41,7 @@ using Clock = std::chrono::steady_clock;
 struct Flight {
     gs_batch* b = nullptr;
     int stream = -1;
+    Clock::time_point started;    // when the worker launched the batch
     uint64_t bytes = 0;
     std::vector<uint64_t> tickets;
     std::vector<const gs_plan*> plans;
@@ -85,6 +86,7 @@ struct gs_server {
     uint64_t inflight_bytes = 0, peak_bytes = 0;
     uint64_t completed = 0, batches = 0, passed = 0;
     uint64_t launches = 0, scans = 0, scan_plans = 0;   // of the completed batches
+    double batch_us = 0.0;        // running mean of the batches' launch-to-completion time
     gs_status fatal = GS_OK;
 };
 
@@ -161,6 +163,9 @@ void worker_loop(gs_server* s) {
                     s->inflight[i]->err = rc;
                     if (rc != GS_OK) s->inflight[i]->msg = last_error();
                     s->inflight_bytes -= s->inflight[i]->bytes;   // its workspaces are done
+                    const double us = std::chrono::duration<double, std::micro>(
+                        Clock::now() - s->inflight[i]->started).count();
+                    s->batch_us = s->batch_us > 0.0 ? 0.8 * s->batch_us + 0.2 * us : us;
                     finished.push_back(s->inflight[i]);
                     s->inflight.erase(s->inflight.begin() + i);
                 } else {
@@ -169,12 +174,16 @@ void worker_loop(gs_server* s) {
             }
             // admission: a new batch starts when the device is idle, when
             // max_batch / 8 queries wait, or when the oldest has waited
-            // max_wait_us; otherwise arrivals gather into the next batch
+            // max_wait_us or half the running mean batch time, whichever is
+            // longer; otherwise arrivals gather into the next batch (a wait
+            // short against the batches in flight costs little latency and
+            // saves the per-batch work of many small batches)
+            const double wait_us = std::max<double>(s->cfg.max_wait_us, 0.5 * s->batch_us);
             const bool ripe =
                 !s->queue.empty() &&
                 (s->inflight.empty() || s->queue.size() >= std::max<uint32_t>(1, s->cfg.max_batch / 8) ||
-                 Clock::now() - s->tickets[s->queue.front()].submitted >=
-                     std::chrono::microseconds(s->cfg.max_wait_us));
+                 std::chrono::duration<double, std::micro>(
+                     Clock::now() - s->tickets[s->queue.front()].submitted).count() >= wait_us);
             while (ripe && !s->queue.empty()) {
                 int st = -1;
                 for (size_t k = 0; k < s->streams.size(); ++k)
@@ -244,6 +253,7 @@ void worker_loop(gs_server* s) {
                     continue;
                 }
                 s->stream_busy[st] = 1;
+                f->started = Clock::now();
                 s->inflight_bytes += bytes;
                 s->peak_bytes = std::max(s->peak_bytes, s->inflight_bytes);
                 s->inflight.push_back(f);
