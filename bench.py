@@ -46,13 +46,15 @@ def _args():
                     help="budget of the CPU oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--mode", default="plain",
-                    choices=["plain", "scan", "batched", "served", "query", "paths"],
+                    choices=["plain", "scan", "batched", "served", "query", "paths", "lspm"],
                     help="plain: the workload's queries one at a time (the headline line); "
                          "scan: the triple scan alone; batched: the batched workload "
                          "(rmat24: 4,096 queries in one launch) against one at a time; "
                          "served: Poisson arrivals into the server on the scale-26 graph; "
                          "query: the workload queries --query picks, one at a time (for "
-                         "profiling single kernels)")
+                         "profiling single kernels); paths: per-path trees against the "
+                         "path-linearized tree; lspm: each query on its per-query LSpM "
+                         "against the full store")
     ap.add_argument("--queries", type=int, default=0,
                     help="batched mode: number of queries (0: the workload's)")
     ap.add_argument("--query", default="0",
@@ -984,6 +986,59 @@ def _scan_roofline(g, w, stream, peaks, which, n_scan=20):
             "ms_median": float(np.median(ms))}
 
 
+def run_lspm(args):
+    """Per-query LSpMs (Sec. 6.2): for each query of the workload (the
+    bandwidth family on rmat26 and with --family bandwidth), the store
+    reduced on the device to the predicates its evaluation reads, its size,
+    the device time of the reduction, and the query's device time on it
+    against the full store (one line; answers checked equal)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2106_14038_b300 as gs
+    w, triples, qs = _workload(args.workload, args.family)
+    g = gs.Graph(*triples, w.n_vertices, w.n_preds)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for i, q in enumerate(qs):
+        plan = g.plan(q.patterns)
+        full_ms, red_ms, build_ms, rows = [], [], [], None
+        for rep in range(args.warmup + args.steps):
+            r = g.eval(plan, stream)
+            n_full = r.info()[0]
+            ms_full = r.stats()[0]
+            r.close()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            lspm = gs.Lspm.for_plan(g, plan, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            r = lspm.eval(plan, stream)
+            n_red = r.info()[0]
+            ms_red = r.stats()[0]
+            r.close()
+            assert n_red == n_full, (i, n_red, n_full)
+            if rep >= args.warmup:
+                full_ms.append(ms_full)
+                red_ms.append(ms_red)
+                build_ms.append(e0.elapsed_time(e1))
+                rows = n_full
+                kept = (lspm.info(False), lspm.info(True))
+            lspm.close()
+        plan.close()
+        out.append({"index": i, "shape": q.shape, "rows": rows,
+                    "kept_rows_entries": kept[0], "kept_cols_entries": kept[1],
+                    "kept_share": (kept[0][1] + kept[1][1]) / (2.0 * g.n_triples),
+                    "full_ms": float(np.median(full_ms)), "lspm_eval_ms": float(np.median(red_ms)),
+                    "lspm_build_ms": float(np.median(build_ms))})
+    print(json.dumps({
+        "metric": "per-query LSpM: device ms of the reduction and of the query on it vs the full store",
+        "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+        "data": "synthetic", "config": {"workload": w.name, "family": args.family,
+                                        "triples": g.n_triples, "queries": len(qs)},
+        "queries": out}), flush=True)
+
+
 def run_paths(args):
     """Per-path binding trees (GS_PLAN_PATHS: one tree per path, tree-pruning,
     join) against the path-linearized tree on the workload's stars,
@@ -1024,6 +1079,9 @@ def main():
     args = _args()
     if args.mode == "paths":
         run_paths(args)
+        return
+    if args.mode == "lspm" and args.impl == "gsmart":
+        run_lspm(args)
         return
     if args.impl == "gsmart" and args.mode == "plain" and args.workload == "rmat26":
         run_bandwidth(args)
