@@ -8,14 +8,16 @@
 // the reduced matrix); Sec. 6.2.2 does the same column-wise (Mc) for the
 // edges evaluated against their direction, each orientation with its own
 // predicate set. Here, per orientation:
-//   1. k_lspm_count: per row, the entries of the set's predicates (a
-//      label-range search per predicate: rows are sorted by (label, other
-//      end)), packed as (count << 32) | (count > 0);
+//   1. k_lspm_count: per row, the entries of the set's predicates (one
+//      pass over a short row's labels, or over a long row's label runs,
+//      each tested against the set's bitmap), packed as
+//      (count << 32) | (count > 0);
 //   2. one device-wide exclusive scan of the packed words gives, per row,
 //      the first entry of the reduced row (high half) and Mr (low half);
-//   3. k_lspm_write: a warp per row copies the kept ranges in label order,
-//      so the reduced rows keep the (label, other end) order, and writes the
-//      compacted row pointers Pr of the kept rows.
+//   3. k_lspm_write: a lane per short row, a warp per long row, copies the
+//      kept entries in label order, so the reduced rows keep the (label,
+//      other end) order, and writes the compacted row pointers Pr of the
+//      kept rows.
 // The reduced orientation is also kept with one row pointer per vertex id
 // (empty rows included) and the triple scan's work items, so the
 // evaluation kernels run on it unchanged.
@@ -37,54 +39,108 @@ struct gs_lspm {
 
 namespace gs {
 
-// Entries of the set's predicates in each row, packed for the scan.
+// The set's predicates as a bitmap in shared memory (P <= 65535), filled
+// by each block from the set's list.
+constexpr uint32_t kKeepWords = 65536 / 32;
+
+__device__ __forceinline__ void load_keep(uint32_t* keep, const uint32_t* __restrict__ set,
+                                          uint32_t n_set) {
+    for (uint32_t w = threadIdx.x; w < kKeepWords; w += blockDim.x) keep[w] = 0;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < n_set; j += blockDim.x)
+        atomicOr(&keep[set[j] >> 5], 1u << (set[j] & 31u));
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool kept_label(const uint32_t* keep, uint32_t l) {
+    return (keep[(l >> 5) & (kKeepWords - 1)] >> (l & 31u)) & 1u;
+}
+
+// Entries of the set's predicates in each row, packed for the scan. A row
+// of at most kDirMin entries is read once, each label tested against the
+// set's bitmap; a longer row is walked run by run through its label
+// directory (one test per run of equal labels).
 __global__ void k_lspm_count(DStore S, uint32_t N, const uint32_t* __restrict__ set, uint32_t n_set,
                              uint64_t* __restrict__ packed) {
+    __shared__ uint32_t keep[kKeepWords];
+    load_keep(keep, set, n_set);
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < N;
          r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = ld(S.ptr + r), e = ld(S.ptr + r + 1);
         uint64_t c = 0;
-        if (ld(S.ptr + r + 1) > ld(S.ptr + r))
-            for (uint32_t j = 0; j < n_set; ++j) {
-                uint32_t lo, len;
-                label_range(S, (uint32_t)r, set[j], lo, len);
-                c += len;
-            }
+        if (e - b <= kDirMin || !S.dir_off) {
+            for (uint32_t i = b; i < e; ++i) c += kept_label(keep, ld(S.lab + i));
+        } else {
+            const uint32_t d0 = ld(S.dir_off + r), d1 = ld(S.dir_off + r + 1);
+            for (uint32_t j = d0; j < d1; ++j)
+                if (kept_label(keep, ld(S.dir_lab + j)))
+                    c += (j + 1 < d1 ? ld(S.dir_pos + j + 1) : e) - ld(S.dir_pos + j);
+        }
         packed[r] = (c << 32) | (c ? 1u : 0u);
     }
 }
 
-// A warp per row: the kept ranges, label by label (the set is sorted), into
-// the reduced arrays; row pointers per vertex id and, for kept rows, the
-// compacted ones.
+// Each warp takes 32 consecutive rows: a lane copies the kept entries of
+// its row when the row has at most kDirMin entries; the rows longer than
+// that are then copied by the whole warp, one after the other, run by run
+// from their label directory. Kept entries stay in (label, other end)
+// order. Row pointers per vertex id, Mr and, for kept rows, the compacted
+// pointers Pr are written on the way.
 __global__ void k_lspm_write(DStore S, uint32_t N, const uint32_t* __restrict__ set, uint32_t n_set,
                              const uint64_t* __restrict__ packed, uint32_t* __restrict__ ptr,
                              uint32_t* __restrict__ mr, uint32_t* __restrict__ pr,
                              uint32_t* __restrict__ idx, uint32_t* __restrict__ lab) {
+    __shared__ uint32_t keep[kKeepWords];
+    load_keep(keep, set, n_set);
     const uint32_t lane = lane_id();
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t r = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < N; r += warps) {
-        const uint64_t pk = packed[r];
-        const uint32_t base = (uint32_t)(pk >> 32);
-        const uint32_t m = (uint32_t)pk;
-        if (lane == 0) { ptr[r] = base; mr[r] = m; }
-        if (ld(S.ptr + r + 1) == ld(S.ptr + r)) continue;
-        uint32_t at = base;
-        bool any = false;
-        for (uint32_t j0 = 0; j0 < n_set; j0 += 32) {
-            uint32_t lo = 0, len = 0;
-            if (j0 + lane < n_set) label_range(S, (uint32_t)r, set[j0 + lane], lo, len);
-            for (uint32_t j = 0; j < 32 && j0 + j < n_set; ++j) {
-                const uint32_t l0 = __shfl_sync(0xffffffffu, lo, j);
-                const uint32_t n0 = __shfl_sync(0xffffffffu, len, j);
-                for (uint32_t t = lane; t < n0; t += 32) {
-                    idx[at + t] = __ldg(S.idx + l0 + t);
-                    lab[at + t] = __ldg(S.lab + l0 + t);
-                }
-                at += n0;
-                any |= n0 > 0;
-            }
+    for (uint64_t r0 = (blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < N;
+         r0 += warps * 32) {
+        const uint64_t r = r0 + lane;
+        const bool valid = r < N;
+        uint32_t b = 0, e = 0, base = 0, m = 0;
+        if (valid) {
+            const uint64_t pk = packed[r];
+            base = (uint32_t)(pk >> 32);
+            m = (uint32_t)pk;
+            b = ld(S.ptr + r);
+            e = ld(S.ptr + r + 1);
+            ptr[r] = base;
+            mr[r] = m;
         }
-        if (any && lane == 0) pr[m] = base;
+        const bool lng = valid && e - b > kDirMin && S.dir_off;
+        if (valid && !lng) {
+            uint32_t at = base;
+            for (uint32_t i = b; i < e; ++i) {
+                const uint32_t l = ld(S.lab + i);
+                if (kept_label(keep, l)) {
+                    idx[at] = ld(S.idx + i);
+                    lab[at] = l;
+                    ++at;
+                }
+            }
+            if (at > base) pr[m] = base;
+        }
+        for (uint32_t longs = __ballot_sync(0xffffffffu, lng); longs; longs &= longs - 1) {
+            const uint32_t k = __ffs(longs) - 1;
+            const uint32_t rr = (uint32_t)(r0 + k);
+            const uint32_t ek = __shfl_sync(0xffffffffu, e, k);
+            const uint32_t bk = __shfl_sync(0xffffffffu, base, k);
+            const uint32_t mk = __shfl_sync(0xffffffffu, m, k);
+            const uint32_t d0 = ld(S.dir_off + rr), d1 = ld(S.dir_off + rr + 1);
+            uint32_t at = bk;
+            for (uint32_t j = d0; j < d1; ++j) {
+                const uint32_t l = ld(S.dir_lab + j);
+                if (!kept_label(keep, l)) continue;
+                const uint32_t lo = ld(S.dir_pos + j), hi = j + 1 < d1 ? ld(S.dir_pos + j + 1) : ek;
+                for (uint32_t t = lane; t < hi - lo; t += 32) {
+                    idx[at + t] = ld(S.idx + lo + t);
+                    lab[at + t] = l;
+                }
+                at += hi - lo;
+            }
+            if (at > bk && lane == 0) pr[mk] = bk;
+        }
     }
 }
 
