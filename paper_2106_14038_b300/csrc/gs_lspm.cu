@@ -14,10 +14,11 @@
 //      (count << 32) | (count > 0);
 //   2. one device-wide exclusive scan of the packed words gives, per row,
 //      the first entry of the reduced row (high half) and Mr (low half);
-//   3. k_lspm_write: a lane per short row, a warp per long row, copies the
-//      kept entries in label order, so the reduced rows keep the (label,
-//      other end) order, and writes the compacted row pointers Pr of the
-//      kept rows.
+//   3. k_lspm_write: a warp per 32 rows copies their kept entries in
+//      order (a stream compaction over runs of short rows, run by run
+//      through the label directory for long rows), so the reduced rows keep
+//      the (label, other end) order, and writes the compacted row pointers
+//      Pr of the kept rows.
 // The reduced orientation is also kept with one row pointer per vertex id
 // (empty rows included) and the triple scan's work items, so the
 // evaluation kernels run on it unchanged.
@@ -69,7 +70,14 @@ __global__ void k_lspm_count(DStore S, uint32_t N, const uint32_t* __restrict__ 
         const uint32_t b = ld(S.ptr + r), e = ld(S.ptr + r + 1);
         uint64_t c = 0;
         if (e - b <= kDirMin || !S.dir_off) {
-            for (uint32_t i = b; i < e; ++i) c += kept_label(keep, ld(S.lab + i));
+            for (uint32_t i = b; i < e; i += 4) {   // four loads in flight (label 0 is never kept)
+                const uint32_t l0 = ld(S.lab + i);
+                const uint32_t l1 = i + 1 < e ? ld(S.lab + i + 1) : 0u;
+                const uint32_t l2 = i + 2 < e ? ld(S.lab + i + 2) : 0u;
+                const uint32_t l3 = i + 3 < e ? ld(S.lab + i + 3) : 0u;
+                c += kept_label(keep, l0) + kept_label(keep, l1) + kept_label(keep, l2) +
+                     kept_label(keep, l3);
+            }
         } else {
             const uint32_t d0 = ld(S.dir_off + r), d1 = ld(S.dir_off + r + 1);
             for (uint32_t j = d0; j < d1; ++j)
@@ -80,24 +88,29 @@ __global__ void k_lspm_count(DStore S, uint32_t N, const uint32_t* __restrict__ 
     }
 }
 
-// Each warp takes 32 consecutive rows: a lane copies the kept entries of
-// its row when the row has at most kDirMin entries; the rows longer than
-// that are then copied by the whole warp, one after the other, run by run
-// from their label directory. Kept entries stay in (label, other end)
-// order. Row pointers per vertex id, Mr and, for kept rows, the compacted
-// pointers Pr are written on the way.
+// Each warp takes 32 consecutive rows. Their kept entries are contiguous in
+// the output and in the same order as in the store, so the warp copies
+// them as a stream compaction: runs of consecutive rows of at most kDirMin
+// entries are one contiguous entry range, read 32 entries at a time (a
+// ballot and a population count place each kept entry), and a longer row
+// is copied run by run from its label directory (runs of predicates
+// outside the set are skipped). Row pointers per vertex id, Mr and, for
+// kept rows, the compacted pointers Pr are written on the way.
 __global__ void k_lspm_write(DStore S, uint32_t N, const uint32_t* __restrict__ set, uint32_t n_set,
-                             const uint64_t* __restrict__ packed, uint32_t* __restrict__ ptr,
-                             uint32_t* __restrict__ mr, uint32_t* __restrict__ pr,
-                             uint32_t* __restrict__ idx, uint32_t* __restrict__ lab) {
+                             const uint64_t* __restrict__ packed, uint32_t nnz,
+                             uint32_t* __restrict__ ptr, uint32_t* __restrict__ mr,
+                             uint32_t* __restrict__ pr, uint32_t* __restrict__ idx,
+                             uint32_t* __restrict__ lab) {
     __shared__ uint32_t keep[kKeepWords];
     load_keep(keep, set, n_set);
     const uint32_t lane = lane_id();
+    const uint32_t below = (1u << lane) - 1u;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t r0 = (blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < N;
          r0 += warps * 32) {
+        const uint32_t nr = N - r0 < 32 ? (uint32_t)(N - r0) : 32u;   // rows of this block
         const uint64_t r = r0 + lane;
-        const bool valid = r < N;
+        const bool valid = lane < nr;
         uint32_t b = 0, e = 0, base = 0, m = 0;
         if (valid) {
             const uint64_t pk = packed[r];
@@ -108,27 +121,46 @@ __global__ void k_lspm_write(DStore S, uint32_t N, const uint32_t* __restrict__ 
             ptr[r] = base;
             mr[r] = m;
         }
-        const bool lng = valid && e - b > kDirMin && S.dir_off;
-        if (valid && !lng) {
-            uint32_t at = base;
-            for (uint32_t i = b; i < e; ++i) {
-                const uint32_t l = ld(S.lab + i);
-                if (kept_label(keep, l)) {
-                    idx[at] = ld(S.idx + i);
-                    lab[at] = l;
-                    ++at;
+        // the next row's first output position: the row's kept entries end there
+        uint32_t next = __shfl_down_sync(0xffffffffu, base, 1);
+        if (lane == nr - 1) next = r0 + nr < N ? (uint32_t)(packed[r0 + nr] >> 32) : nnz;
+        if (valid && next > base) pr[m] = base;
+        const uint32_t longs = __ballot_sync(0xffffffffu, valid && e - b > kDirMin && S.dir_off);
+        uint32_t at = __shfl_sync(0xffffffffu, base, 0);
+        uint32_t k = 0;
+        while (k < nr) {
+            // rows k .. kl - 1 are short: one contiguous entry range
+            const uint32_t rest = longs & ~((1u << k) - 1u);
+            const uint32_t kl = rest ? (uint32_t)(__ffs(rest) - 1) : nr;
+            if (kl > k) {
+                const uint32_t x0 = __shfl_sync(0xffffffffu, b, k);
+                const uint32_t x1 = __shfl_sync(0xffffffffu, e, kl - 1);
+                for (uint32_t i0 = x0; i0 < x1; i0 += 128) {   // four loads in flight per lane
+                    uint32_t l[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t i = i0 + 32u * (uint32_t)u + lane;
+                        l[u] = i < x1 ? ld(S.lab + i) : 0u;   // label 0 is never kept
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t i = i0 + 32u * (uint32_t)u + lane;
+                        const bool kp = kept_label(keep, l[u]);
+                        const uint32_t mask = __ballot_sync(0xffffffffu, kp);
+                        if (kp) {
+                            const uint32_t o = at + __popc(mask & below);
+                            idx[o] = ld(S.idx + i);
+                            lab[o] = l[u];
+                        }
+                        at += __popc(mask);
+                    }
                 }
             }
-            if (at > base) pr[m] = base;
-        }
-        for (uint32_t longs = __ballot_sync(0xffffffffu, lng); longs; longs &= longs - 1) {
-            const uint32_t k = __ffs(longs) - 1;
-            const uint32_t rr = (uint32_t)(r0 + k);
-            const uint32_t ek = __shfl_sync(0xffffffffu, e, k);
-            const uint32_t bk = __shfl_sync(0xffffffffu, base, k);
-            const uint32_t mk = __shfl_sync(0xffffffffu, m, k);
+            if (kl >= nr) break;
+            // row kl is long: its kept runs, one after the other
+            const uint32_t rr = (uint32_t)(r0 + kl);
+            const uint32_t ek = __shfl_sync(0xffffffffu, e, kl);
             const uint32_t d0 = ld(S.dir_off + rr), d1 = ld(S.dir_off + rr + 1);
-            uint32_t at = bk;
             for (uint32_t j = d0; j < d1; ++j) {
                 const uint32_t l = ld(S.dir_lab + j);
                 if (!kept_label(keep, l)) continue;
@@ -139,7 +171,7 @@ __global__ void k_lspm_write(DStore S, uint32_t N, const uint32_t* __restrict__ 
                 }
                 at += hi - lo;
             }
-            if (at > bk && lane == 0) pr[mk] = bk;
+            k = kl + 1;
         }
     }
 }
@@ -174,7 +206,7 @@ gs_status build_side(gs_lspm* L, int dir, cudaStream_t st) {
     if (e == cudaSuccess && !preds.empty())
         e = cudaMemcpyAsync(set, preds.data(), sizeof(uint32_t) * preds.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return done(cuda_fail(e, "gs_lspm_build"));
-    k_lspm_count<<<nb, kThreads, 0, st>>>(dview(F), N, set, (uint32_t)preds.size(), packed);
+    k_lspm_count<<<g->sm_count * 6, kThreads, 0, st>>>(dview(F), N, set, (uint32_t)preds.size(), packed);
     k_block_sums_u64<<<nb, kThreads, 0, st>>>(packed, n_dev, bsum, nullptr);
     k_scan_block_sums<<<1, kThreads, 0, st>>>(bsum, boff, (uint32_t)nb, total, nullptr);
     k_scan_apply_u64<<<nb, kThreads, 0, st>>>(packed, n_dev, boff, nullptr);
@@ -204,8 +236,8 @@ gs_status build_side(gs_lspm* L, int dir, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(L->mr[dir] + N, &tail[1], 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L->pr[dir] + kept, &tail[0], 4, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return done(cuda_fail(e, "gs_lspm_build"));
-    k_lspm_write<<<nb, kThreads, 0, st>>>(dview(F), N, set, (uint32_t)preds.size(), packed, R.ptr,
-                                          L->mr[dir], L->pr[dir], R.idx, R.lab);
+    k_lspm_write<<<g->sm_count * 6, kThreads, 0, st>>>(dview(F), N, set, (uint32_t)preds.size(), packed,
+                                          (uint32_t)nnz, R.ptr, L->mr[dir], L->pr[dir], R.idx, R.lab);
     e = cudaGetLastError();
     if (e != cudaSuccess) return done(cuda_fail(e, "gs_lspm_build"));
     rc = store_items(g, R, nnz, st);   // synchronizes st
