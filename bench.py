@@ -841,6 +841,27 @@ def run_bandwidth(args):
     plain_q, _ = aggregate_rate(float(np.sum(pl_ms)), len(qs) * args.steps, ws, dist)
     lat_ms = 1000 * np.array(lat)
     rows = [int(g.eval(pl, stream).info()[0]) for pl in plans]
+    # one traced pass (untimed): device ms per phase of each query, setup +
+    # triple scan, the binding-tree levels and the enumeration
+    g.set_trace(True)
+    phases = []
+    for pl in plans:
+        r = g.eval(pl, stream)
+        r.info()
+        try:
+            ph = r.phases()
+            phases.append((ph[0], float(sum(ph[1:-1])), ph[-1]))
+        except gs.GsError:   # a query the single-CTA kernel finished has none
+            pass
+        r.close()
+    g.set_trace(False)
+    phase_summary = None
+    if phases:
+        a = np.array(phases)
+        phase_summary = {"queries": len(phases), "setup_and_scan_ms": float(a[:, 0].mean()),
+                         "levels_ms": float(a[:, 1].mean()), "enumerate_ms": float(a[:, 2].mean()),
+                         "how": "one traced pass, untimed: CUDA events between the phases "
+                                "of each query (mean over queries)"}
 
     # batched: all queries in one launch per step, autotuned on them
     bcfg, tune_ms = g.autotune_batch(plans, stream)
@@ -921,7 +942,8 @@ def run_bandwidth(args):
             "plain": {"value": plain_q, "unit": "queries/s",
                       "p50_ms": float(np.percentile(lat_ms, 50)),
                       "p99_ms": float(np.percentile(lat_ms, 99)),
-                      "timing": "CUDA events around each pass of the queries, one at a time"},
+                      "timing": "CUDA events around each pass of the queries, one at a time",
+                      "phases": phase_summary},
             "batched": {"value": b_q, "unit": "queries/s", "ms_per_step": float(np.mean(b_ms)),
                         "config": bcfg.as_dict(), "autotune_best_ms": tune_ms,
                         "triple_scans_per_step": b_scans[0], "scan_plans_per_step": b_scans[1],
