@@ -399,7 +399,9 @@ def run_gsmart(args):
     scan_ms = 0.0
     for _ in range(n_scan):
         flush.fill_(1)
-        torch.cuda._sleep(400000)   # ~0.2 ms on the device: the host enqueues the scan meanwhile
+        # ~2 ms on the device: the host enqueues the scan meanwhile, so no
+        # host delay falls between the two events
+        torch.cuda._sleep(4000000)
         se0.record(stream)
         g.scan(preds, dirs, out=out)
         se1.record(stream)
@@ -516,7 +518,9 @@ def run_scan_only(args):
         for _ in range(args.steps):
             torch.cuda.synchronize()
             flush.fill_(1)
-            torch.cuda._sleep(400000)   # ~0.2 ms on the device: the host enqueues the scan meanwhile
+            # ~2 ms on the device: the host enqueues the scan meanwhile, so no
+            # host delay falls between the two events
+            torch.cuda._sleep(4000000)
             e0.record(stream)
             g.scan(preds, dirs, out=out)
             e1.record(stream)
@@ -988,7 +992,9 @@ def _scan_roofline(g, w, stream, peaks, which, n_scan=20):
     ms = []
     for _ in range(n_scan):
         flush.fill_(1)
-        torch.cuda._sleep(400000)   # ~0.2 ms on the device: the host enqueues the scan meanwhile
+        # ~2 ms on the device: the host enqueues the scan meanwhile, so no
+        # host delay falls between the two events
+        torch.cuda._sleep(4000000)
         se0.record(stream)
         g.scan(preds, dirs, out=out)
         se1.record(stream)
