@@ -291,13 +291,14 @@ def test_workspace_retry(rmat14, monkeypatch, exec_path):
 
 
 def test_hub_graph_expansion(exec_path):
-    # one hub with 80000 out-edges: load-balanced expansion over a huge range;
-    # through the constant it also exceeds the single-block budget (escalation)
+    # one hub with 120,000 out-edges (past 10^5): load-balanced expansion over
+    # a huge range; through the constant it also exceeds the single-block
+    # budget (escalation)
     rng = np.random.default_rng(9)
-    n_v = 90000
-    s = np.concatenate([np.zeros(80000, np.int64), rng.integers(0, n_v, 60000)])
-    o = np.concatenate([np.arange(1, 80001), rng.integers(0, n_v, 60000)])
-    p = np.concatenate([np.ones(80000, np.int64), rng.integers(1, 4, 60000)])
+    n_v = 130000
+    s = np.concatenate([np.zeros(120000, np.int64), rng.integers(0, n_v, 60000)])
+    o = np.concatenate([np.arange(1, 120001), rng.integers(0, n_v, 60000)])
+    p = np.concatenate([np.ones(120000, np.int64), rng.integers(1, 4, 60000)])
     g, ix = _graph(s, p, o, n_v, 3)
     _same(g, ix, [(0, 1, -1), (-1, 2, -2)])
     _same(g, ix, [(0, 1, -1)])
