@@ -610,3 +610,38 @@ def test_plain_and_batched_rmat22_workload_equal_oracle():
         assert np.array_equal(b.fetch(i), want), i
     b.close()
     g.close()
+
+
+def test_invariance_under_pattern_order_renaming_and_planner(rmat14):
+    # the answer set does not depend on the order of the patterns, the names
+    # of the variables (columns follow the renaming) or the planner and
+    # evaluation mode; every row satisfies every pattern
+    w, (s, p, o), g, ix = rmat14
+    sm = rdfgen.Sampler(s, p, o, w.n_vertices, w.n_preds)
+    pats = [q.patterns for q in rdfgen.queries(w, sm)]
+    for i, sh in enumerate([rdfgen.cycle(4), rdfgen.snowflake([2, 1]), rdfgen.chain(4)]):
+        pats.append(sm.sample(sh, 123, i, 2e5).patterns)
+    sm.close()
+    triples = set(zip(s.tolist(), p.tolist(), o.tolist()))
+    rng = np.random.default_rng(31)
+    for pt in pats:
+        pt = np.asarray(pt, np.int64)
+        base = g.query(pt)
+        k = base.shape[1]
+        for row in base[:200]:   # every row satisfies every pattern
+            for a, pr, b in pt:
+                sa = row[-a - 1] if a < 0 else a
+                sb = row[-b - 1] if b < 0 else b
+                assert (int(sa), int(pr), int(sb)) in triples
+        for _ in range(2):
+            perm = rng.permutation(k)                  # variable j -> perm[j]
+            q = pt[rng.permutation(len(pt))].copy()
+            for c in (0, 2):
+                m = q[:, c] < 0
+                q[m, c] = -(perm[-q[m, c] - 1] + 1)
+            got = g.query(q)
+            back = got[:, perm]                        # column perm[j] holds variable j
+            order = np.lexsort(back.T[::-1])
+            assert np.array_equal(back[order], base), pt
+        for flags in (gs.PLAN_DIRECTION, gs.PLAN_LISTS, gs.PLAN_PATHS):
+            assert np.array_equal(g.query(pt, flags=flags), base), (pt, flags)
